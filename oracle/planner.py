@@ -1,0 +1,253 @@
+"""Cache-blocking transpiler, oracle side (test infrastructure only).
+
+Restates Sec. IV.A (Listing 3) of Doi & Horii step by step in the paper's names, with the
+readings below for the points the paper leaves silent or garbled.  The CUDA library has its
+own C++ implementation; the two must produce the same schedule bit for bit.
+
+Algorithm (logical qubit -> physical bit map ``m``, inverse ``pinv``):
+
+  REMAINING <- gate sequence (SWAP gates removed as relabels, see below)
+  while REMAINING is not empty:                       # "until ... not empty" read as "until empty"
+    choose QB_CHUNK: c - reserve logical qubits       # "QB_CHUNK[nc-1]" read as nc entries, reserve = 0
+        priority: (1) qubits of the first remaining gate, (2) qubits of multi-qubit gates in
+        list order, (3) qubits of 1-qubit gates in list order, (4) qubits already resident
+        (physical < c) by ascending physical bit; a gate whose new qubits do not all fit is
+        skipped ("all the qubits used in a multi-qubit gate should be placed in a chunk at the
+        same time", Sec. IV.A).
+    put chunk_swap gates in OUTPUT                    # one swap round
+        incoming chosen qubits (physical >= c) sorted by logical id are paired with vacated
+        physical bits (< c, held by unchosen qubits) sorted ascending; each pair is
+        chunk_swap(slot, old_position) (Sec. IV.C, Fig. 10 case (a)).
+    clear QB_BLOCKED
+    for gate in REMAINING:
+      if all its qubits in QB_CHUNK and none in QB_BLOCKED: put gate in OUTPUT (block)
+      else: put gate in REMAINING_NEXT; if some of its qubits are in QB_CHUNK, set all of its
+            qubits in QB_BLOCKED            # the listing's "set QB_CHUNK" read as QB_BLOCKED
+    REMAINING <- REMAINING_NEXT
+
+SWAP gates are relabels: a SWAP(a, b) in the input exchanges which virtual qubit carries labels
+a and b; later gates are rewritten, no data moves.  At the end the output is reordered so that
+physical bit q holds logical qubit q (Sec. IV.C: "reorder qubits for the output", Fig. 10 case
+(b)).  That reordering is a bit permutation, written as two rounds of disjoint transpositions:
+for each cycle x0 -> x1 -> ... (x0 its smallest bit, x_{i+1} = destination of x_i) the first
+round exchanges x_i <-> x_{L-i} and the second x_i <-> x_{L+1-i} (indices mod L).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+
+@dataclass
+class Plan:
+    n: int
+    c: int
+    reserve: int
+    restore_layout: bool
+    ops: list = field(default_factory=list)  # ("swap"|"unpermute", [(p, q)]) / ("block", [(gi, phys)])
+    final_map: list = field(default_factory=list)  # physical bit of each logical qubit at the end
+
+    def serialize(self):
+        """Integer stream used to compare schedules bit for bit with the library's planner."""
+        out = [self.n, self.c, self.reserve, int(self.restore_layout), len(self.ops)]
+        for kind, body in self.ops:
+            if kind in ("swap", "unpermute"):
+                out += [1 if kind == "swap" else 3, len(body)]
+                for p, q in body:
+                    out += [p, q]
+            else:
+                out += [2, len(body)]
+                for gi, phys in body:
+                    out += [gi, len(phys), phys[0], phys[1] if len(phys) > 1 else -1]
+        out += list(self.final_map)
+        return out
+
+    @property
+    def n_blocks(self):
+        return sum(1 for k, _ in self.ops if k == "block")
+
+    @property
+    def n_swap_rounds(self):
+        return sum(1 for k, _ in self.ops if k == "swap")
+
+    @property
+    def n_unpermute_rounds(self):
+        return sum(1 for k, _ in self.ops if k == "unpermute")
+
+
+def _canonical_qubits(kind, qubits):
+    """Logical qubits of a gate in ascending order (the schedule lists physical bits in this
+    order)."""
+    return tuple(sorted(qubits))
+
+
+def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True) -> Plan:
+    if not (1 <= n <= 62):
+        raise ValueError("n out of range")
+    if c < 1:
+        raise ValueError("c must be >= 1")
+    if reserve not in (0, 1):
+        raise ValueError("reserve must be 0 or 1")
+    width = min(c, n)  # physical bits 0 .. width-1 form a chunk
+    target = min(c - reserve, n)
+    if target < 1:
+        raise ValueError("chunk too small")
+
+    # SWAP gates as relabels: lab[label] = virtual qubit carrying that label.
+    lab = list(range(n))
+    remaining = []  # (gate index, virtual qubits ascending by label order of description)
+    for gi, (kind, qubits, _params) in enumerate(gates):
+        for q in qubits:
+            if not (0 <= q < n):
+                raise ValueError(f"gate {gi} qubit {q} out of range")
+        if len(set(qubits)) != len(qubits):
+            raise ValueError(f"gate {gi} repeats a qubit")
+        if kind == "swap":
+            a, b = qubits
+            lab[a], lab[b] = lab[b], lab[a]
+            continue
+        vq = tuple(lab[q] for q in _canonical_qubits(kind, qubits))
+        if len(vq) > target:
+            raise ValueError(f"gate {gi} is wider than the chunk")
+        remaining.append((gi, vq))
+
+    m = list(range(n))  # virtual (logical) qubit -> physical bit
+    pinv = list(range(n))  # physical bit -> virtual qubit
+    plan = Plan(n=n, c=c, reserve=reserve, restore_layout=restore_layout)
+
+    while remaining:
+        # -- choose QB_CHUNK
+        chosen = []
+        chosen_set = set()
+
+        def try_add(qs):
+            new = []
+            for q in qs:
+                if q not in chosen_set and q not in new:
+                    new.append(q)
+            if len(chosen) + len(new) <= target:
+                chosen.extend(new)
+                chosen_set.update(new)
+
+        try_add(remaining[0][1])
+        for _gi, qs in remaining:
+            if len(chosen) >= target:
+                break
+            if len(qs) > 1:
+                try_add(qs)
+        for _gi, qs in remaining:
+            if len(chosen) >= target:
+                break
+            if len(qs) == 1:
+                try_add(qs)
+        for p in range(width):
+            if len(chosen) >= target:
+                break
+            try_add((pinv[p],))
+
+        # -- chunk_swap round
+        incoming = sorted(q for q in chosen if m[q] >= width)
+        vacated = sorted(p for p in range(width) if pinv[p] not in chosen_set)
+        pairs = []
+        for q_in, slot in zip(incoming, vacated):
+            old = m[q_in]
+            q_out = pinv[slot]
+            m[q_in], pinv[slot] = slot, q_in
+            m[q_out], pinv[old] = old, q_out
+            pairs.append((slot, old))
+        if pairs:
+            plan.ops.append(("swap", pairs))
+
+        # -- scan REMAINING with QB_BLOCKED
+        blocked = set()
+        block = []
+        nxt = []
+        for gi, qs in remaining:
+            if all(q in chosen_set for q in qs) and not any(q in blocked for q in qs):
+                block.append((gi, tuple(m[q] for q in qs)))
+            else:
+                nxt.append((gi, qs))
+                if any(q in chosen_set for q in qs):
+                    blocked.update(qs)
+        plan.ops.append(("block", block))
+        remaining = nxt
+
+    # -- output reordering: physical bit m[lab[q]] must end at bit q.
+    src = [m[lab[q]] for q in range(n)]
+    if restore_layout:
+        dest = [0] * n
+        for q in range(n):
+            dest[src[q]] = q
+        r1, r2 = [], []
+        seen = [False] * n
+        for x0 in range(n):
+            if seen[x0]:
+                continue
+            cyc = [x0]
+            seen[x0] = True
+            y = dest[x0]
+            while y != x0:
+                cyc.append(y)
+                seen[y] = True
+                y = dest[y]
+            L = len(cyc)
+            if L == 1:
+                continue
+            for i in range(1, (L - 1) // 2 + 1):
+                a, b = cyc[i], cyc[L - i]
+                r1.append((min(a, b), max(a, b)))
+            for i in range(1, L // 2 + 1):
+                a, b = cyc[i], cyc[(L + 1 - i) % L]
+                r2.append((min(a, b), max(a, b)))
+        for r in (r1, r2):
+            if r:
+                plan.ops.append(("unpermute", sorted(r)))
+        plan.final_map = list(range(n))
+    else:
+        plan.final_map = src
+    return plan
+
+
+def validate(plan: Plan, gates) -> None:
+    """Raise AssertionError unless the plan is a valid cache-blocked schedule of `gates`:
+    every non-SWAP gate is emitted exactly once, every emitted gate's physical bits are < c,
+    every swap round pairs a bit < c with a bit >= c and no bit twice, and the per-qubit gate
+    order of the input is preserved."""
+    n, c = plan.n, plan.c
+    width = min(c, n)
+    emitted = []
+    for kind, body in plan.ops:
+        if kind == "swap":
+            used = set()
+            for p, q in body:
+                assert p < width <= q < n, (p, q)
+                assert p not in used and q not in used
+                used.update((p, q))
+        elif kind == "unpermute":
+            used = set()
+            for p, q in body:
+                assert 0 <= p < q < n
+                assert p not in used and q not in used
+                used.update((p, q))
+        else:
+            assert len(body) > 0, "empty block"
+            for gi, phys in body:
+                assert all(0 <= p < width for p in phys), phys
+                emitted.append(gi)
+    expect = [gi for gi, g in enumerate(gates) if g[0] != "swap"]
+    assert sorted(emitted) == expect, "each gate exactly once"
+    # per-qubit order: for each logical label track positions through relabels
+    lab = list(range(n))
+    vq_of = {}
+    for gi, (kind, qubits, _p) in enumerate(gates):
+        if kind == "swap":
+            a, b = qubits
+            lab[a], lab[b] = lab[b], lab[a]
+        else:
+            vq_of[gi] = tuple(lab[q] for q in qubits)
+    pos = {gi: k for k, gi in enumerate(emitted)}
+    last = {}
+    for gi in expect:
+        for v in vq_of[gi]:
+            if v in last:
+                assert pos[last[v]] < pos[gi], f"order violated on qubit {v}"
+            last[v] = gi

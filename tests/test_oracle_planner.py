@@ -1,0 +1,134 @@
+"""Pins for the oracle's cache-blocking planner (Sec. IV.A Listing 3, Sec. IV.C Fig. 10), no GPU.
+
+The paper's worked example (Fig. 9) is an unavailable image, so the swap count is parity
+unpinned; the schedule is pinned by a hand-worked example, validity and simulation
+equivalence."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from oracle import planner, sim
+
+
+def _read_plan_golden(path):
+    ops, meta = [], {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] == "op":
+                kind = parts[1]
+                if kind in ("swap", "unpermute"):
+                    ops.append((kind, [tuple(int(v) for v in p.split(",")) for p in parts[2:]]))
+                else:
+                    body = []
+                    for p in parts[2:]:
+                        gi, phys = p.split(":")
+                        body.append((int(gi), tuple(int(v) for v in phys.split(","))))
+                    ops.append(("block", body))
+            else:
+                meta[parts[0]] = parts[1:]
+    gates = []
+    for g in meta["gates"]:
+        kind, qs = g.split(":")
+        gates.append((kind, tuple(int(v) for v in qs.split(",")), ()))
+    return int(meta["n"][0]), int(meta["c"][0]), gates, ops
+
+
+def test_hand_worked_schedule(golden_dir):
+    n, c, gates, ops = _read_plan_golden(os.path.join(golden_dir, "planner_n4_c2.txt"))
+    p = planner.plan_blocking(n, gates, c)
+    assert p.ops == ops
+    assert p.final_map == list(range(n))
+
+
+def _circuits(n, seed):
+    return [
+        cg.random_layers(n, 4, seed),
+        cg.quantum_volume(n, 4, seed),
+        cg.qft(n),
+        cg.qft(n, with_swaps=False),
+        cg.hea(n, 2, seed, 0),
+        cg.noisy_trajectory(n, 3, 0.2, seed, 1),
+    ]
+
+
+@pytest.mark.parametrize("n,c", [(4, 2), (5, 3), (7, 4), (8, 8), (9, 3), (10, 6), (12, 5), (6, 12)])
+@pytest.mark.parametrize("reserve", [0, 1])
+def test_validity_and_equivalence(n, c, reserve):
+    if c - reserve < 2:
+        pytest.skip("chunk narrower than a 2-qubit gate")
+    for i, gates in enumerate(_circuits(n, 10 * n + c)):
+        p = planner.plan_blocking(n, gates, c, reserve=reserve)
+        planner.validate(p, gates)
+        ref = sim.simulate(n, gates, 5 % (1 << n))
+        got = sim.execute_plan(n, gates, p, 5 % (1 << n))
+        assert np.abs(ref - got).max() < 1e-12, (i, n, c)
+
+
+@pytest.mark.parametrize("n,c", [(6, 3), (9, 4), (11, 5)])
+def test_keep_layout_map(n, c):
+    gates = cg.random_layers(n, 3, 7) + [("swap", (0, n - 1), ())] + cg.quantum_volume(n, 2, 8)
+    p_keep = planner.plan_blocking(n, gates, c, restore_layout=False)
+    planner.validate(p_keep, gates)
+    assert p_keep.n_unpermute_rounds == 0
+    got = sim.execute_plan(n, gates, p_keep, 3)
+    # logical qubit q sits on physical bit final_map[q]: gather it back
+    idx = np.arange(1 << n)
+    phys = np.zeros_like(idx)
+    for q in range(n):
+        phys |= ((idx >> q) & 1) << p_keep.final_map[q]
+    ref = sim.simulate(n, gates, 3)
+    assert np.abs(got[phys] - ref).max() < 1e-12
+
+
+def test_no_swaps_when_state_fits_chunk():
+    gates = cg.random_layers(6, 5, 1)
+    p = planner.plan_blocking(6, gates, 10)
+    assert p.n_swap_rounds == 0 and p.n_blocks == 1 and p.n_unpermute_rounds == 0
+
+
+def test_unpermute_is_at_most_two_rounds_and_restores():
+    # any final bit permutation is undone by <= 2 rounds of disjoint transpositions
+    n = 7
+    for perm in itertools.islice(itertools.permutations(range(n)), 0, 5040, 97):
+        gates = []
+        # build the permutation from SWAP relabels (bubble sort)
+        cur = list(range(n))
+        target = list(perm)
+        for i in range(n):
+            j = cur.index(target[i])
+            while j > i:
+                gates.append(("swap", (j - 1, j), ()))
+                cur[j - 1], cur[j] = cur[j], cur[j - 1]
+                j -= 1
+        gates.append(("h", (0,), ()))
+        p = planner.plan_blocking(n, gates, 3)
+        assert p.n_unpermute_rounds <= 2
+        ref = sim.simulate(n, gates, 77)
+        assert np.abs(sim.execute_plan(n, gates, p, 77) - ref).max() < 1e-13
+
+
+def test_first_gate_always_progresses():
+    # every iteration emits at least the first remaining gate -> blocks never empty
+    gates = cg.quantum_volume(10, 6, 3)
+    p = planner.plan_blocking(10, gates, 2)
+    assert all(len(b) >= 1 for k, b in p.ops if k == "block")
+    assert p.n_blocks <= len(gates)
+
+
+def test_gate_wider_than_chunk_rejected():
+    with pytest.raises(ValueError):
+        planner.plan_blocking(5, [("cx", (0, 1), ())], 2, reserve=1)
+
+
+def test_swap_counts_shrink_with_bigger_chunks():
+    gates = cg.quantum_volume(16, 10, 2)
+    counts = [planner.plan_blocking(16, gates, c).n_swap_rounds for c in (4, 8, 12, 16)]
+    assert counts == sorted(counts, reverse=True) and counts[-1] == 0
