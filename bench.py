@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the cache-blocked state-vector simulator on GB300.
+
+Workload (default): quantum-volume circuit, n = 30 qubits, depth 30 (450 Haar SU(4) gates),
+complex64 state (8 GiB), chunk c = 13.  One step = build the gate records, plan the cache
+blocking (host), reset the state to |0..0>, apply the circuit on the cache-blocked path, and
+read the norm back.  Metric: gates per second (higher is better), plus effective HBM bandwidth
+= (blocking sweeps + permutation sweeps) x 2 x 2^n x 8 B / time.
+
+Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle on a bounded sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates/s (cache-blocked path), n=30 complex64 quantum volume"
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return PEAK_FALLBACK_GBS, "fallback"
+
+
+def _workload(name):
+    import circuitgen as cg
+    w = dict(cg.WORKLOADS[name])
+    w["desc"] = cg.build(name)
+    return w
+
+
+# ------------------------------------------------------------------ clock sampling
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class _Barrier:
+    def __init__(self, world, device):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=device)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def cpu_oracle_rate(w, budget_s: float = 12.0, max_gates: int = 60):
+    """Gates/s of the CPU oracle (complex128, all host cores) on a bounded prefix of the workload:
+    gates are applied one by one until `budget_s` seconds of work or `max_gates` gates."""
+    from oracle import sim
+    n = w["n"]
+    state = sim.basis_state(n, 0)
+    done = 0
+    t0 = time.perf_counter()
+    for g in w["desc"][:max_gates]:
+        sim.apply(state, n, [g])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    del state
+    return done / dt, done, dt, sim.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.workload)
+    from oracle import sim
+    n = w["n"]
+    per_step = max(1, args.ref_gates_per_step)
+    state = sim.basis_state(n, 0)
+    gates = w["desc"]
+    pos = 0
+
+    def step():
+        nonlocal pos
+        for _ in range(per_step):
+            sim.apply(state, n, [gates[pos % len(gates)]])
+            pos += 1
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    rate = args.steps * per_step / dt
+    sample = (f"{per_step} gates per step of the n={n} workload in complex128 (first "
+              f"{args.steps * per_step + args.warmup * per_step} gates incl. warm-up), one pass per gate")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "gates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(w),
+        "cpu_baseline": {"value": rate, "unit": "gates/s", "cores": sim.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(w):
+    return {"workload": f"{args_workload_name(w)}", "n": w["n"], "gates": len(w["desc"]), "chunk_bits": w["c"],
+            "state": "complex64", "l2": "state 8 GiB >> 129 MB L2 (no flush needed)"}
+
+
+def args_workload_name(w):
+    kinds = {"quantum_volume": "quantum volume", "random_layers": "random layers", "qft": "QFT"}
+    depth = f" depth {w['depth']}" if "depth" in w else ""
+    return f"{kinds[w['kind']]} n={w['n']}{depth}, {len(w['desc'])} gates, complex64, chunk c={w['c']}"
+
+
+def _traffic_for(kernel_src: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(os.path.join(ROOT, kernel_src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    e = d.get(workload, {}).get(os.path.basename(kernel_src))
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ main GPU benchmark
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    bar = _Barrier(world, torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    bar.barrier()
+    import paper_2102_02957_gb300 as sv
+
+    w = _workload(args.workload)
+    n, c, desc = w["n"], w["c"], w["desc"]
+    G = len(desc)
+    stream = torch.cuda.Stream()
+    st = sv.StateVector(n, "c64", stream=stream)
+    st.set_profiling(True)
+    sweep_bytes = 2.0 * (1 << n) * 8
+
+    def step():
+        gates = sv.make_gates(desc)
+        plan = sv.Plan(n, gates, chunk_bits=c)
+        st.init_basis(0)
+        st.apply(gates, plan)
+        nrm = st.norm2()
+        return nrm, plan
+
+    for _ in range(args.warmup):
+        step()
+    st.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    bar.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    ms_block = ms_perm = 0.0
+    n_block = n_perm = launches = 0
+    norm_last = None
+    for _ in range(args.steps):
+        norm_last, plan = step()
+        s = st.stats()
+        ms_block += s.ms_block
+        ms_perm += s.ms_permute
+        n_block += s.sweeps_block
+        n_perm += s.sweeps_permute
+        launches += s.kernel_launches + 2  # + init (set-one kernel) + norm reduction
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    bar.barrier()
+    ck = clocks.stop()
+    elapsed_ms = bar.max(t_start.elapsed_time(t_end))
+    ms_step = elapsed_ms / args.steps
+    value = world * G * args.steps / (elapsed_ms / 1000.0)
+    info = plan.info()
+    sweeps_per_step = info.n_blocks + info.n_swap_rounds + info.n_unpermute_rounds
+    eff_gbs = sweeps_per_step * sweep_bytes / (ms_step / 1000.0) / 1e9
+    peak, peak_kind = _peaks()
+
+    blk_ms = ms_block / max(1, n_block)
+    perm_ms = ms_perm / max(1, n_perm)
+    blk_gbs = sweep_bytes / (blk_ms / 1000.0) / 1e9
+    perm_gbs = sweep_bytes / (perm_ms / 1000.0) / 1e9
+    dominant = "k_block" if ms_block >= ms_perm else "k_permute"
+    dom_src = "paper_2102_02957_gb300/csrc/k_block.cu" if dominant == "k_block" else \
+        "paper_2102_02957_gb300/csrc/k_permute.cu"
+    achieved = blk_gbs if dominant == "k_block" else perm_gbs
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": _traffic_for(dom_src, args.workload),
+                "algorithmic_bytes_per_launch": sweep_bytes,
+                "launch_ms": blk_ms if dominant == "k_block" else perm_ms,
+                "k_block": {"launches_per_step": info.n_blocks, "ms": blk_ms, "GBs": blk_gbs,
+                            "share": ms_block / (ms_block + ms_perm)},
+                "k_permute": {"launches_per_step": info.n_swap_rounds + info.n_unpermute_rounds, "ms": perm_ms,
+                              "GBs": perm_gbs, "share": ms_perm / (ms_block + ms_perm)}}
+
+    # plain per-gate GPU path on the same workload (the paper's baseline)
+    gates = sv.make_gates(desc)
+    st.init_basis(0)
+    st.apply(gates)
+    st.synchronize()
+    pg_steps = max(1, min(2, args.steps))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pg_steps):
+        st.init_basis(0)
+        st.apply(gates)
+        st.norm2()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pg_ms = e0.elapsed_time(e1) / pg_steps
+    s = st.stats()
+    per_gate = {"gates_per_s": G / (pg_ms / 1000.0), "ms_per_step": pg_ms,
+                "effective_GBs": G * sweep_bytes / (pg_ms / 1000.0) / 1e9,
+                "kernel_GBs": G * sweep_bytes / (s.ms_gate / 1000.0) / 1e9 if s.ms_gate else None}
+
+    # end to end through the C ABI with host buffers: H2D of the input state, plan, apply,
+    # D2H of the output state
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.zeros(2 << n, dtype=torch.float32).pin_memory()
+        h_in[0] = 1.0
+        h_out = torch.empty(2 << n, dtype=torch.float32).pin_memory()
+        gates = sv.make_gates(desc)
+        plan = sv.Plan(n, gates, chunk_bits=c)
+
+        def e2e_step():
+            g = sv.make_gates(desc)
+            p = sv.Plan(n, g, chunk_bits=c)
+            st.set_state(h_in.data_ptr())
+            st.apply(g, p)
+            st.get_state(h_out.data_ptr())
+
+        e2e_step()
+        k2 = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        bar.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        dt = bar.max(time.perf_counter() - t0)
+        out0 = h_out[:2].numpy().copy()
+        e2e = {"value": world * G * k2 / dt, "unit": "gates/s", "h2d_bytes_per_step": int((2 << n) * 4),
+               "d2h_bytes_per_step": int((2 << n) * 4), "ms_per_step": 1000 * dt / k2}
+        del h_in, h_out
+        _ = out0
+
+    st.close()
+    torch.cuda.synchronize()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, done, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {done} gates of the same workload applied to an n={n} complex128 state "
+                         f"({dt:.1f} s, one pass per gate)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
+            "effective_hbm_GBs": eff_gbs, "effective_hbm_frac": eff_gbs / peak,
+            "sweeps_per_step": {"blocks": info.n_blocks, "swap_rounds": info.n_swap_rounds,
+                                "reorder_rounds": info.n_unpermute_rounds},
+            "per_gate": per_gate, "speedup_vs_per_gate": pg_ms / ms_step,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+            "gpu_launches": launches, "norm": norm_last,
+        }
+        print(json.dumps(line), flush=True)
+    bar.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qv30")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-gates-per-step", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

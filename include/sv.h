@@ -1,0 +1,193 @@
+/* sv.h -- C ABI of the GB300 cache-blocked state-vector simulator.
+ *
+ * Method: Doi & Horii, "Cache Blocking Technique to Large Scale Quantum Computing Simulation
+ * on Supercomputers" (arXiv 2102.02957).  An n-qubit state is 2^n complex amplitudes, index
+ * bit k = qubit k (Sec. II.A, Fig. 1-2).  A transpiler (Sec. IV.A, Listing 3) inserts
+ * chunk_swap gates so that runs of gates touch only the low c "chunk" bits; each run is then
+ * applied chunk by chunk (Sec. IV.C, Listing 4).  On one GPU the chunk is staged once from
+ * HBM into shared memory per run, and every chunk_swap round is one in-place HBM permutation
+ * pass.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an sv_status; nothing throws across the ABI.  On failure
+ *    sv_last_error() returns a message for the calling thread (valid until its next call).
+ *  - Pointers are plain host pointers unless a parameter says "device".  The library never
+ *    takes ownership of caller memory; objects it creates (sv_handle, sv_plan_h) are freed
+ *    by the matching destroy/free call.
+ *  - Qubit numbering is little-endian (Sec. II.A: |2> = |10>).
+ *  - Calls that launch GPU work are asynchronous on the handle's stream unless they return
+ *    host data (readouts, sv_get_state), which synchronise that stream before returning.
+ *  - Sizes: 1 <= n <= 34.  A gate acts on 1 or 2 distinct qubits < n.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sv_status {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,         /* invalid argument (null pointer, size or qubit out of range)   */
+    SV_ERR_OOM = 2,         /* device or host allocation failed                               */
+    SV_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed                    */
+    SV_ERR_PLAN = 4,        /* plan does not match the state / gate list, or planning failed   */
+    SV_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired; the state is undefined      */
+    SV_ERR_UNSUPPORTED = 6  /* valid request that this build does not implement                */
+} sv_status;
+
+typedef enum sv_dtype {
+    SV_C64 = 1,  /* complex64: interleaved (float re, float im), 8 bytes per amplitude    */
+    SV_C128 = 2  /* complex128: interleaved (double re, double im), 16 bytes per amplitude */
+} sv_dtype;
+
+/* One gate.  nq = 1 or 2 qubits q[0] (, q[1]).  m is the row-major 2^nq x 2^nq complex
+ * matrix, interleaved (re, im) doubles, in the local basis b = bit(q[0]) + 2*bit(q[1]);
+ * entries past 2^nq x 2^nq are ignored.  flags: SV_GATE_SWAP marks a SWAP that the planner
+ * applies as a relabel (no data movement; m must still hold the SWAP matrix for the
+ * per-gate path).  SV_GATE_DIAG marks a diagonal matrix (a hint; m is authoritative). */
+enum { SV_GATE_SWAP = 1, SV_GATE_DIAG = 2 };
+typedef struct sv_gate {
+    int32_t nq;
+    int32_t q[2];
+    int32_t flags;
+    double m[32];
+} sv_gate;
+
+/* Gate kinds for sv_gate_make. params: U3 (theta, phi, lambda) per Sec. II.A Eq. 1 (the
+ * paper's psi is phi); RY/RZ (theta); CP (phi); UNITARY1/UNITARY2 take 8/32 doubles of a
+ * row-major interleaved matrix.  qubits: CX and CP and CZ take (control, target); the CX
+ * matrix is Eq. 2 with the control as the higher local bit. */
+typedef enum sv_gate_kind {
+    SV_K_UNITARY1 = 0, SV_K_UNITARY2 = 1, SV_K_U3 = 2, SV_K_CX = 3, SV_K_H = 4, SV_K_X = 5,
+    SV_K_Y = 6, SV_K_Z = 7, SV_K_RY = 8, SV_K_RZ = 9, SV_K_CP = 10, SV_K_CZ = 11, SV_K_SWAP = 12
+} sv_gate_kind;
+
+/* Build one gate record (gate matrices of Sec. II.A, Eq. 1 and Eq. 2; host FP64).
+ * qubits: 1 or 2 entries by kind.  params: as listed above (NULL allowed for kinds without
+ * parameters).  out: filled on success.  SV_ERR_ARG for an unknown kind or repeated qubit. */
+sv_status sv_gate_make(int32_t kind, const int32_t *qubits, const double *params, sv_gate *out);
+
+/* Planner / executor options.  Defaults from sv_options_default(). */
+typedef struct sv_options {
+    int32_t chunk_bits;     /* c: physical bits 0..c-1 form a chunk (Sec. II.B, IV.A); default 13 */
+    int32_t reserve;        /* 0: chunk holds c chosen qubits; 1: c-1 (the listing's "nc-1"). default 0 */
+    int32_t restore_layout; /* 1: end with the output reordering of Sec. IV.C (Fig. 10 (b)). default 1 */
+    int32_t seg_bits;       /* register-group width used inside a chunk (4); fusion width on TC path */
+    int32_t use_tc;         /* 1: apply fused groups as 3xTF32 tensor-core contractions (complex64) */
+    int32_t use_model;      /* 1: let a trained cost model steer QB_CHUNK choices (sv_costmodel_*) */
+    int32_t threads;        /* consumer threads per chunk CTA; 0 = auto                             */
+    int32_t reserved[9];
+} sv_options;
+
+void sv_options_default(sv_options *opts);
+
+/* ------------------------------------------------------------------ state handles */
+typedef struct sv_state *sv_handle;
+
+/* Create an n-qubit state of `dtype`.  dev_buf: caller-owned DEVICE buffer of at least
+ * 2^n * bytes-per-amplitude bytes, 256-byte aligned (e.g. a torch tensor); NULL lets the
+ * library allocate (freed by sv_destroy).  cuda_stream: a cudaStream_t, or NULL for the
+ * legacy default stream.  The amplitudes are undefined until sv_init_basis/sv_set_state. */
+sv_status sv_create(int32_t n, int32_t dtype, void *dev_buf, size_t bytes, void *cuda_stream,
+                    sv_handle *out);
+sv_status sv_destroy(sv_handle h);
+
+/* Set the state to the basis state |basis_index> (Sec. IV.C: zero every chunk, one
+ * amplitude = 1).  basis_index < 2^n. */
+sv_status sv_init_basis(sv_handle h, uint64_t basis_index);
+
+/* Copy the 2^n amplitudes to / from HOST memory (pinned memory gives full bandwidth).
+ * Layout as sv_dtype.  Synchronous with respect to the host. */
+sv_status sv_get_state(sv_handle h, void *host_out);
+sv_status sv_set_state(sv_handle h, const void *host_in);
+
+/* Device pointer of the amplitude array (borrowed; valid until sv_destroy). */
+sv_status sv_device_ptr(sv_handle h, void **dev_ptr);
+sv_status sv_synchronize(sv_handle h);
+
+/* ------------------------------------------------------------------ planning */
+typedef struct sv_plan *sv_plan_h;
+
+/* Cache-blocking transpiler of Sec. IV.A (Listing 3) on the host.  Deterministic: the same
+ * input gives the same schedule.  Uses opts->chunk_bits, reserve, restore_layout (and
+ * use_model if a cost model is loaded).  SV_ERR_ARG when a gate is wider than the chunk. */
+sv_status sv_plan_blocking(int32_t n, const sv_gate *gates, int64_t n_gates,
+                           const sv_options *opts, sv_plan_h *out);
+sv_status sv_plan_free(sv_plan_h plan);
+
+typedef struct sv_plan_info {
+    int32_t n, chunk_bits, reserve, restore_layout;
+    int32_t n_blocks;            /* blocking sections (one HBM sweep each)           */
+    int32_t n_swap_rounds;       /* chunk_swap rounds (one in-place pass each)       */
+    int32_t n_unpermute_rounds;  /* output-reordering rounds (0..2)                  */
+    int32_t n_segments;          /* register groups over all blocks                  */
+    int64_t n_gates_emitted;     /* gates inside blocks (SWAP relabels excluded)     */
+    int32_t final_map[64];       /* physical bit of logical qubit q after the plan   */
+} sv_plan_info;
+sv_status sv_plan_get_info(sv_plan_h plan, sv_plan_info *info);
+
+/* Integer serialisation of the schedule (used to compare schedules bit for bit):
+ * [n, c, reserve, restore, n_ops, ops..., final_map[n]] with ops
+ *   [1, r, (p, q) x r]                 chunk_swap round (p < c <= q)
+ *   [2, G, (gate_index, nq, p0, p1) x G]  block; p0/p1 = physical bits of the gate's qubits in
+ *                                         ascending logical order, p1 = -1 for 1 qubit
+ *   [3, r, (p, q) x r]                 output-reordering round.
+ * Writes at most `cap` values to buf; *len receives the full length (call with cap 0 to
+ * size the buffer). */
+sv_status sv_plan_serialize(sv_plan_h plan, int64_t *buf, int64_t cap, int64_t *len);
+
+/* ------------------------------------------------------------------ execution */
+/* Apply the circuit.  plan == NULL: the plain per-gate path (one HBM sweep per gate, the
+ * paper's baseline of Sec. V.A).  Otherwise the cache-blocked path (Listing 4): each chunk_swap
+ * round is one in-place permutation pass and each blocking section one pass in which every
+ * chunk is staged in shared memory, all its gates applied, and written back.  The plan must
+ * have been made from the same n and gate list (SV_ERR_PLAN otherwise). */
+sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, sv_plan_h plan);
+
+/* Statistics of the last sv_apply_circuit on this handle (host-side counts). */
+typedef struct sv_apply_stats {
+    int64_t kernel_launches;
+    int64_t sweeps_block;       /* blocked-section passes                */
+    int64_t sweeps_permute;     /* chunk_swap + reordering passes        */
+    int64_t sweeps_gate;        /* per-gate passes                       */
+    double algorithmic_bytes;   /* (passes) x 2 x 2^n x bytes/amplitude  */
+    double ms_block;            /* device time of the blocked-section kernels (profiling on) */
+    double ms_permute;          /* device time of the permutation kernels (profiling on)     */
+    double ms_gate;             /* device time of the per-gate kernels (profiling on)        */
+} sv_apply_stats;
+/* Counts of the last sv_apply_circuit; with profiling on, also the summed device time of its
+ * kernels by kind, taken from CUDA events recorded on the handle's stream around each launch
+ * (this call then synchronises the stream). */
+sv_status sv_get_apply_stats(sv_handle h, sv_apply_stats *out);
+
+/* on != 0: record CUDA events around every kernel that sv_apply_circuit launches. */
+sv_status sv_set_profiling(sv_handle h, int32_t on);
+
+/* ------------------------------------------------------------------ readouts (FP64 accumulate) */
+/* Measurement probabilities |a_i|^2 (Sec. II.A) for all 2^n indices.  out: 2^n doubles,
+ * on the device when out_on_device != 0, else on the host. */
+sv_status sv_probabilities(sv_handle h, double *out, int32_t out_on_device);
+
+/* Sum of |a_i|^2. */
+sv_status sv_norm2(sv_handle h, double *out);
+
+/* Draw `shots` basis indices by inverse CDF: shot s is the smallest i with
+ * sum_{k<=i} |a_k|^2 > u_s * sum_k |a_k|^2, u_s the s-th uniform of the SplitMix64 stream
+ * seeded with `seed` (top 53 bits * 2^-53).  out: `shots` uint64 on the host. */
+sv_status sv_sample(sv_handle h, int64_t shots, uint64_t seed, uint64_t *out);
+
+/* <psi| P |psi> for the Pauli word P = i^{popcount(x&z)} X^x Z^z (Y where both bits are set).
+ * out[0] = real part, out[1] = imaginary part (host). */
+sv_status sv_expval_pauli(sv_handle h, uint64_t x_mask, uint64_t z_mask, double *out);
+
+/* Thread-local message for the last failed call on this thread ("" if none). */
+const char *sv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_H */

@@ -1,0 +1,180 @@
+"""GB300 cache-blocked state-vector simulator (Doi & Horii, arXiv 2102.02957) -- Python binding.
+
+Every step runs in the CUDA library libsv.so through its C ABI (include/sv.h); this module only
+marshals arguments.  PyTorch is used for device memory and streams when the caller passes a
+tensor buffer; it is not needed otherwise."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (GATE_DTYPE, SV_C64, SV_C128, SV_GATE_DIAG, SV_GATE_SWAP, SVError, check, lib,  # noqa: F401
+                   sv_apply_stats, sv_options, sv_plan_info)
+
+_KIND = {"u3": _lib.SV_K_U3, "cx": _lib.SV_K_CX, "h": _lib.SV_K_H, "x": _lib.SV_K_X, "y": _lib.SV_K_Y,
+         "z": _lib.SV_K_Z, "ry": _lib.SV_K_RY, "rz": _lib.SV_K_RZ, "cp": _lib.SV_K_CP, "cz": _lib.SV_K_CZ,
+         "swap": _lib.SV_K_SWAP}
+
+DTYPES = {"c64": SV_C64, "c128": SV_C128, SV_C64: SV_C64, SV_C128: SV_C128}
+
+
+def make_gates(descriptions) -> np.ndarray:
+    """Gate records (sv_gate array) from (kind, qubits, params) descriptions, each built by
+    sv_gate_make in the library."""
+    L = lib()
+    out = np.zeros(len(descriptions), dtype=GATE_DTYPE)
+    q = (ctypes.c_int32 * 2)()
+    for i, (kind, qubits, params) in enumerate(descriptions):
+        for j, v in enumerate(qubits):
+            q[j] = int(v)
+        if kind == "unitary":
+            m = np.ascontiguousarray(params[0], dtype=np.complex128)
+            k = _lib.SV_K_UNITARY1 if m.shape == (2, 2) else _lib.SV_K_UNITARY2
+            p = np.ascontiguousarray(m.reshape(-1).view(np.float64))
+        else:
+            k = _KIND[kind]
+            p = np.ascontiguousarray(np.asarray(params, dtype=np.float64)) if params else None
+        pp = p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p is not None and p.size else None
+        check(L.sv_gate_make(k, q, pp, out[i:i + 1].ctypes.data))
+    return out
+
+
+def options(**kw) -> sv_options:
+    o = sv_options()
+    lib().sv_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "restore_layout":
+            v = int(bool(v))
+        setattr(o, k, int(v))
+    return o
+
+
+class Plan:
+    """A cache-blocking schedule made by the library's planner (sv_plan_blocking)."""
+
+    def __init__(self, n: int, gates: np.ndarray, **opts):
+        self._h = ctypes.c_void_p()
+        o = options(**opts)
+        check(lib().sv_plan_blocking(n, gates.ctypes.data, len(gates), ctypes.byref(o), ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> sv_plan_info:
+        inf = sv_plan_info()
+        check(lib().sv_plan_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def serialize(self):
+        ln = ctypes.c_int64()
+        check(lib().sv_plan_serialize(self._h, None, 0, ctypes.byref(ln)))
+        buf = (ctypes.c_int64 * ln.value)()
+        check(lib().sv_plan_serialize(self._h, buf, ln.value, ctypes.byref(ln)))
+        return list(buf)
+
+    def close(self):
+        if self._h:
+            lib().sv_plan_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StateVector:
+    """n-qubit state on the GPU.  `buffer`: optional CUDA torch tensor that holds the amplitudes
+    (caller-owned); `stream`: optional torch.cuda.Stream (or raw cudaStream_t int)."""
+
+    def __init__(self, n: int, dtype="c64", buffer=None, stream=None):
+        self.n = n
+        self.dtype = DTYPES[dtype]
+        self.amp_bytes = 8 if self.dtype == SV_C64 else 16
+        self._buffer = buffer
+        ptr = buffer.data_ptr() if buffer is not None else None
+        nbytes = buffer.numel() * buffer.element_size() if buffer is not None else 0
+        s = getattr(stream, "cuda_stream", stream)
+        self._h = ctypes.c_void_p()
+        check(lib().sv_create(n, self.dtype, ptr, nbytes, s, ctypes.byref(self._h)))
+
+    # -- state
+    def init_basis(self, index: int = 0):
+        check(lib().sv_init_basis(self._h, index))
+
+    def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
+        dt = np.complex64 if self.dtype == SV_C64 else np.complex128
+        if out is None:
+            out = np.empty(1 << self.n, dtype=dt)
+        check(lib().sv_get_state(self._h, out.ctypes.data if isinstance(out, np.ndarray) else out))
+        return out
+
+    def set_state(self, host) -> None:
+        ptr = host.ctypes.data if isinstance(host, np.ndarray) else host
+        check(lib().sv_set_state(self._h, ptr))
+
+    def device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        check(lib().sv_device_ptr(self._h, ctypes.byref(p)))
+        return p.value
+
+    def synchronize(self):
+        check(lib().sv_synchronize(self._h))
+
+    # -- execution
+    def apply(self, gates: np.ndarray, plan: Plan | None = None):
+        check(lib().sv_apply_circuit(self._h, gates.ctypes.data, len(gates), plan.handle if plan else None))
+
+    def set_profiling(self, on: bool = True):
+        check(lib().sv_set_profiling(self._h, int(bool(on))))
+
+    def stats(self) -> sv_apply_stats:
+        s = sv_apply_stats()
+        check(lib().sv_get_apply_stats(self._h, ctypes.byref(s)))
+        return s
+
+    # -- readouts
+    def probabilities(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(1 << self.n, dtype=np.float64)
+        if isinstance(out, np.ndarray):
+            check(lib().sv_probabilities(self._h, out.ctypes.data, 0))
+        else:  # a CUDA torch tensor of float64
+            check(lib().sv_probabilities(self._h, out.data_ptr(), 1))
+        return out
+
+    def norm2(self) -> float:
+        v = ctypes.c_double()
+        check(lib().sv_norm2(self._h, ctypes.byref(v)))
+        return v.value
+
+    def sample(self, shots: int, seed: int) -> np.ndarray:
+        out = np.empty(shots, dtype=np.uint64)
+        check(lib().sv_sample(self._h, shots, seed, out.ctypes.data))
+        return out
+
+    def expval_pauli(self, x_mask: int, z_mask: int) -> complex:
+        v = (ctypes.c_double * 2)()
+        check(lib().sv_expval_pauli(self._h, x_mask, z_mask, v))
+        return complex(v[0], v[1])
+
+    def close(self):
+        if self._h:
+            lib().sv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

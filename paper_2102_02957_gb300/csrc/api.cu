@@ -1,0 +1,555 @@
+// C ABI entry points (include/sv.h): state handles, planning, execution and readouts.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void fail(sv_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) fail(SV_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    fail(SV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int num_sms() {
+    static int cached = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached) {
+        int dev = 0;
+        check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        check_cuda(cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    }
+    return cached;
+}
+
+static size_t amp_bytes(int dtype) { return dtype == SV_C64 ? 8 : 16; }
+
+static void ensure_scratch(sv_state *h, size_t bytes) {
+    if (h->scratch_bytes >= bytes) return;
+    if (h->scratch) {
+        check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        cudaFree(h->scratch);
+        h->scratch = nullptr;
+        h->scratch_bytes = 0;
+    }
+    check_cuda(cudaMalloc(&h->scratch, bytes), "cudaMalloc(scratch)");
+    h->scratch_bytes = bytes;
+}
+
+static void check_dev_error(sv_state *h) {
+    int e = 0;
+    check_cuda(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read error word");
+    check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (e != DEV_OK) {
+        int zero = 0;
+        cudaMemcpy(h->dev_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == DEV_ERR_TIMEOUT) fail(SV_ERR_TIMEOUT, "a bounded device wait expired");
+        fail(SV_ERR_CUDA, "device error word set");
+    }
+}
+
+static void validate_gates(int n, const sv_gate *gates, int64_t n_gates) {
+    if (n_gates < 0 || (n_gates > 0 && !gates)) fail(SV_ERR_ARG, "bad gate list");
+    for (int64_t i = 0; i < n_gates; ++i) {
+        const sv_gate &g = gates[i];
+        if (g.nq != 1 && g.nq != 2) fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": nq must be 1 or 2");
+        for (int j = 0; j < g.nq; ++j)
+            if (g.q[j] < 0 || g.q[j] >= n) fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range");
+        if (g.nq == 2 && g.q[0] == g.q[1]) fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit");
+    }
+}
+
+// Device program of one blocking section.
+struct BlockProg {
+    size_t seg_off, gate_off;
+    int nseg, ngate;
+};
+
+template <typename T>
+static void build_programs(const sv_plan *plan, const sv_gate *gates, std::vector<unsigned char> &host,
+                           std::vector<BlockProg> &progs) {
+    const int width = std::min(plan->c, plan->n);
+    host.clear();
+    progs.clear();
+    auto align = [&](size_t a) {
+        while (host.size() % a) host.push_back(0);
+    };
+    for (const PlanOp &op : plan->ops) {
+        if (op.kind != 2) continue;
+        std::vector<HostSeg> segs = segment_block(op.gates, width);
+        std::vector<DevSeg> dsegs;
+        std::vector<DevGate<T>> dgates;
+        for (const HostSeg &s : segs) {
+            DevSeg d{};
+            for (int k = 0; k < SEG_BITS; ++k) d.pos[k] = s.pos[k];
+            d.g0 = (int32_t)dgates.size();
+            for (int32_t gi : s.gates) {
+                DevGate<T> dg;
+                const BlockGate &bg = op.gates[gi];
+                encode_gate<T>(gates[bg.gi], bg, s, dg);
+                dgates.push_back(dg);
+            }
+            d.g1 = (int32_t)dgates.size();
+            dsegs.push_back(d);
+        }
+        BlockProg bp{};
+        align(256);
+        bp.seg_off = host.size();
+        bp.nseg = (int)dsegs.size();
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(dsegs.data());
+        host.insert(host.end(), p, p + dsegs.size() * sizeof(DevSeg));
+        align(256);
+        bp.gate_off = host.size();
+        bp.ngate = (int)dgates.size();
+        p = reinterpret_cast<const unsigned char *>(dgates.data());
+        host.insert(host.end(), p, p + dgates.size() * sizeof(DevGate<T>));
+        progs.push_back(bp);
+    }
+    align(256);
+}
+
+static void upload_program(sv_state *h, const std::vector<unsigned char> &host) {
+    const size_t bytes = std::max<size_t>(host.size(), 256);
+    if (h->prog_event) check_cuda(cudaEventSynchronize(h->prog_event), "cudaEventSynchronize");
+    if (h->prog_host_bytes < bytes) {
+        if (h->prog_host) cudaFreeHost(h->prog_host);
+        h->prog_host = nullptr;
+        check_cuda(cudaHostAlloc(&h->prog_host, bytes, cudaHostAllocDefault), "cudaHostAlloc(program)");
+        h->prog_host_bytes = bytes;
+    }
+    if (h->prog_bytes < bytes) {
+        if (h->prog) {
+            check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+            cudaFree(h->prog);
+        }
+        h->prog = nullptr;
+        check_cuda(cudaMalloc(&h->prog, bytes), "cudaMalloc(program)");
+        h->prog_bytes = bytes;
+    }
+    if (!host.empty()) {
+        std::memcpy(h->prog_host, host.data(), host.size());
+        check_cuda(cudaMemcpyAsync(h->prog, h->prog_host, host.size(), cudaMemcpyHostToDevice, h->stream),
+                   "upload program");
+    }
+    if (!h->prog_event) check_cuda(cudaEventCreateWithFlags(&h->prog_event, cudaEventDisableTiming), "cudaEventCreate");
+    check_cuda(cudaEventRecord(h->prog_event, h->stream), "cudaEventRecord");
+}
+
+}  // namespace sv
+
+using namespace sv;
+
+#define SV_API_BEGIN try {
+#define SV_API_END                  \
+    return SV_OK;                   \
+    }                               \
+    catch (const sv::Error &e) {    \
+        sv::set_error(e.msg);       \
+        return e.code;              \
+    }                               \
+    catch (const std::bad_alloc &) { \
+        sv::set_error("host allocation failed"); \
+        return SV_ERR_OOM;          \
+    }                               \
+    catch (...) {                   \
+        sv::set_error("unexpected exception"); \
+        return SV_ERR_CUDA;         \
+    }
+
+extern "C" {
+
+const char *sv_last_error(void) { return g_last_error.c_str(); }
+
+void sv_options_default(sv_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->chunk_bits = 13;
+    o->reserve = 0;
+    o->restore_layout = 1;
+    o->seg_bits = SEG_BITS;
+    o->use_tc = 0;
+    o->use_model = 0;
+    o->threads = 0;
+}
+
+sv_status sv_create(int32_t n, int32_t dtype, void *dev_buf, size_t bytes, void *cuda_stream, sv_handle *out) {
+    SV_API_BEGIN
+    if (!out) fail(SV_ERR_ARG, "sv_create: out is null");
+    *out = nullptr;
+    if (n < 1 || n > 34) fail(SV_ERR_ARG, "sv_create: n must be in [1, 34]");
+    if (dtype != SV_C64 && dtype != SV_C128) fail(SV_ERR_ARG, "sv_create: unknown dtype");
+    const size_t need = (size_t(1) << n) * amp_bytes(dtype);
+    std::unique_ptr<sv_state> h(new sv_state());
+    h->n = n;
+    h->dtype = dtype;
+    h->stream = (cudaStream_t)cuda_stream;
+    check_cuda(cudaGetDevice(&h->device), "cudaGetDevice");
+    if (dev_buf) {
+        if (bytes < need) fail(SV_ERR_ARG, "sv_create: buffer smaller than 2^n amplitudes");
+        if (reinterpret_cast<uintptr_t>(dev_buf) % 256) fail(SV_ERR_ARG, "sv_create: buffer not 256-byte aligned");
+        h->amp = dev_buf;
+        h->owns_amp = false;
+    } else {
+        check_cuda(cudaMalloc(&h->amp, need), "cudaMalloc(state)");
+        h->owns_amp = true;
+    }
+    check_cuda(cudaMalloc(&h->dev_err, sizeof(int)), "cudaMalloc(error word)");
+    check_cuda(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream), "cudaMemsetAsync");
+    *out = h.release();
+    SV_API_END
+}
+
+sv_status sv_destroy(sv_handle h) {
+    SV_API_BEGIN
+    if (!h) return SV_OK;
+    cudaStreamSynchronize(h->stream);
+    if (h->owns_amp && h->amp) cudaFree(h->amp);
+    if (h->dev_err) cudaFree(h->dev_err);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->prog) cudaFree(h->prog);
+    if (h->prog_host) cudaFreeHost(h->prog_host);
+    if (h->prog_event) cudaEventDestroy(h->prog_event);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+    SV_API_END
+}
+
+sv_status sv_init_basis(sv_handle h, uint64_t basis) {
+    SV_API_BEGIN
+    if (!h) fail(SV_ERR_ARG, "null handle");
+    if (basis >> h->n) fail(SV_ERR_ARG, "sv_init_basis: index out of range");
+    launch_init_basis(h->dtype, h->amp, h->n, basis, h->stream);
+    SV_API_END
+}
+
+sv_status sv_get_state(sv_handle h, void *host_out) {
+    SV_API_BEGIN
+    if (!h || !host_out) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    check_cuda(cudaMemcpyAsync(host_out, h->amp, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(D2H)");
+    check_dev_error(h);
+    SV_API_END
+}
+
+sv_status sv_set_state(sv_handle h, const void *host_in) {
+    SV_API_BEGIN
+    if (!h || !host_in) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    check_cuda(cudaMemcpyAsync(h->amp, host_in, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(H2D)");
+    check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    SV_API_END
+}
+
+sv_status sv_device_ptr(sv_handle h, void **p) {
+    SV_API_BEGIN
+    if (!h || !p) fail(SV_ERR_ARG, "null argument");
+    *p = h->amp;
+    SV_API_END
+}
+
+sv_status sv_synchronize(sv_handle h) {
+    SV_API_BEGIN
+    if (!h) fail(SV_ERR_ARG, "null handle");
+    check_dev_error(h);
+    SV_API_END
+}
+
+sv_status sv_plan_blocking(int32_t n, const sv_gate *gates, int64_t n_gates, const sv_options *opts, sv_plan_h *out) {
+    SV_API_BEGIN
+    if (!out) fail(SV_ERR_ARG, "out is null");
+    *out = nullptr;
+    sv_options o;
+    if (opts) o = *opts; else sv_options_default(&o);
+    *out = plan_blocking(n, gates, n_gates, o);
+    SV_API_END
+}
+
+sv_status sv_plan_free(sv_plan_h p) {
+    SV_API_BEGIN
+    delete p;
+    SV_API_END
+}
+
+sv_status sv_plan_get_info(sv_plan_h p, sv_plan_info *info) {
+    SV_API_BEGIN
+    if (!p || !info) fail(SV_ERR_ARG, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = p->n;
+    info->chunk_bits = p->c;
+    info->reserve = p->reserve;
+    info->restore_layout = p->restore;
+    for (const PlanOp &op : p->ops) {
+        if (op.kind == 1) ++info->n_swap_rounds;
+        if (op.kind == 2) { ++info->n_blocks; info->n_gates_emitted += (int64_t)op.gates.size(); }
+        if (op.kind == 3) ++info->n_unpermute_rounds;
+    }
+    info->n_segments = p->n_segments;
+    for (int q = 0; q < p->n && q < 64; ++q) info->final_map[q] = p->final_map[q];
+    SV_API_END
+}
+
+sv_status sv_plan_serialize(sv_plan_h p, int64_t *buf, int64_t cap, int64_t *len) {
+    SV_API_BEGIN
+    if (!p || !len) fail(SV_ERR_ARG, "null argument");
+    std::vector<int64_t> v{p->n, p->c, p->reserve, p->restore, (int64_t)p->ops.size()};
+    for (const PlanOp &op : p->ops) {
+        v.push_back(op.kind);
+        if (op.kind == 2) {
+            v.push_back((int64_t)op.gates.size());
+            for (const BlockGate &g : op.gates) {
+                v.push_back(g.gi);
+                v.push_back(g.nq);
+                if (g.nq == 1) {
+                    v.push_back(g.phys[0]);
+                    v.push_back(-1);
+                } else {  // ascending logical (label) order
+                    const bool swap = g.label[0] > g.label[1];
+                    v.push_back(swap ? g.phys[1] : g.phys[0]);
+                    v.push_back(swap ? g.phys[0] : g.phys[1]);
+                }
+            }
+        } else {
+            v.push_back((int64_t)op.pairs.size());
+            for (auto pq : op.pairs) {
+                v.push_back(pq.first);
+                v.push_back(pq.second);
+            }
+        }
+    }
+    for (int32_t x : p->final_map) v.push_back(x);
+    *len = (int64_t)v.size();
+    if (buf && cap > 0) std::memcpy(buf, v.data(), sizeof(int64_t) * (size_t)std::min<int64_t>(cap, *len));
+    SV_API_END
+}
+
+// Timing marks around launches (profiling mode): kind 0 = per-gate, 1 = block, 2 = permute.
+static void mark_begin(sv_state *h, int kind) {
+    if (!h->profiling) return;
+    const size_t need = 2 * (h->ev_marks.size() + 1);
+    while (h->ev_pool.size() < need) {
+        cudaEvent_t e;
+        check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+        h->ev_pool.push_back(e);
+    }
+    const int idx = (int)(2 * h->ev_marks.size());
+    check_cuda(cudaEventRecord(h->ev_pool[idx], h->stream), "cudaEventRecord");
+    h->ev_marks.emplace_back(kind, idx);
+}
+
+static void mark_end(sv_state *h) {
+    if (!h->profiling) return;
+    check_cuda(cudaEventRecord(h->ev_pool[h->ev_marks.back().second + 1], h->stream), "cudaEventRecord");
+}
+
+sv_status sv_set_profiling(sv_handle h, int32_t on) {
+    SV_API_BEGIN
+    if (!h) fail(SV_ERR_ARG, "null handle");
+    h->profiling = on != 0;
+    SV_API_END
+}
+
+sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, sv_plan_h plan) {
+    SV_API_BEGIN
+    if (!h) fail(SV_ERR_ARG, "null handle");
+    validate_gates(h->n, gates, n_gates);
+    if (h->profiling && !h->ev_marks.empty() && !h->stats_timed)
+        check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");  // events about to be reused
+    h->ev_marks.clear();
+    h->stats_timed = false;
+    sv_apply_stats st{};
+    const double sweep = 2.0 * (double)(int64_t(1) << h->n) * (double)amp_bytes(h->dtype);
+    if (!plan) {
+        for (int64_t i = 0; i < n_gates; ++i) {
+            mark_begin(h, 0);
+            launch_gate(h->dtype, h->amp, h->n, gates[i], h->stream);
+            mark_end(h);
+            ++st.kernel_launches;
+            ++st.sweeps_gate;
+        }
+    } else {
+        if (plan->n != h->n) fail(SV_ERR_PLAN, "plan was made for another qubit count");
+        if ((int64_t)plan->keys.size() != n_gates) fail(SV_ERR_PLAN, "plan was made for another gate list");
+        for (int64_t i = 0; i < n_gates; ++i) {
+            const GateKey k{gates[i].nq, gates[i].q[0], gates[i].nq == 2 ? gates[i].q[1] : -1, gates[i].flags};
+            if (!(k == plan->keys[(size_t)i])) fail(SV_ERR_PLAN, "gate " + std::to_string(i) + " differs from the planned list");
+        }
+        std::vector<unsigned char> host;
+        std::vector<BlockProg> progs;
+        if (h->dtype == SV_C64) build_programs<float>(plan, gates, host, progs);
+        else build_programs<double>(plan, gates, host, progs);
+        upload_program(h, host);
+        size_t bi = 0;
+        const unsigned char *base = static_cast<const unsigned char *>(h->prog);
+        for (const PlanOp &op : plan->ops) {
+            if (op.kind == 2) {
+                const BlockProg &bp = progs[bi++];
+                mark_begin(h, 1);
+                launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.seg_off, bp.nseg, base + bp.gate_off,
+                             bp.ngate, h->dev_err, 0, h->stream);
+                mark_end(h);
+                ++st.sweeps_block;
+            } else {
+                mark_begin(h, 2);
+                launch_permute(h->dtype, h->amp, h->n, op.pairs, h->stream);
+                mark_end(h);
+                ++st.sweeps_permute;
+            }
+            ++st.kernel_launches;
+        }
+    }
+    st.algorithmic_bytes = sweep * (double)(st.sweeps_block + st.sweeps_permute + st.sweeps_gate);
+    h->stats = st;
+    SV_API_END
+}
+
+sv_status sv_get_apply_stats(sv_handle h, sv_apply_stats *out) {
+    SV_API_BEGIN
+    if (!h || !out) fail(SV_ERR_ARG, "null argument");
+    if (h->profiling && !h->ev_marks.empty() && !h->stats_timed) {
+        check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        double ms[3] = {0, 0, 0};
+        for (auto km : h->ev_marks) {
+            float t = 0;
+            check_cuda(cudaEventElapsedTime(&t, h->ev_pool[km.second], h->ev_pool[km.second + 1]),
+                       "cudaEventElapsedTime");
+            ms[km.first] += t;
+        }
+        h->stats.ms_gate = ms[0];
+        h->stats.ms_block = ms[1];
+        h->stats.ms_permute = ms[2];
+        h->stats_timed = true;
+    }
+    *out = h->stats;
+    SV_API_END
+}
+
+sv_status sv_probabilities(sv_handle h, double *out, int32_t on_device) {
+    SV_API_BEGIN
+    if (!h || !out) fail(SV_ERR_ARG, "null argument");
+    const int64_t len = int64_t(1) << h->n;
+    if (on_device) {
+        launch_probs(h->dtype, h->amp, h->n, out, 0, len, h->stream);
+        check_dev_error(h);
+    } else {
+        const int64_t piece = std::min<int64_t>(len, int64_t(1) << 24);
+        ensure_scratch(h, (size_t)piece * sizeof(double));
+        for (int64_t first = 0; first < len; first += piece) {
+            launch_probs(h->dtype, h->amp, h->n, h->scratch, first, piece, h->stream);
+            check_cuda(cudaMemcpyAsync(out + first, h->scratch, (size_t)piece * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream), "cudaMemcpyAsync(probabilities)");
+        }
+        check_dev_error(h);
+    }
+    SV_API_END
+}
+
+static int reduce_blocks(int n) {
+    const int64_t len = int64_t(1) << n;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 8, len / 256));
+}
+
+sv_status sv_norm2(sv_handle h, double *out) {
+    SV_API_BEGIN
+    if (!h || !out) fail(SV_ERR_ARG, "null argument");
+    const int nb = reduce_blocks(h->n);
+    ensure_scratch(h, (size_t)nb * sizeof(double));
+    launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb, h->stream);
+    std::vector<double> part((size_t)nb);
+    check_cuda(cudaMemcpyAsync(part.data(), h->scratch, nb * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync(partials)");
+    check_dev_error(h);
+    double s = 0;
+    for (double v : part) s += v;
+    *out = s;
+    SV_API_END
+}
+
+sv_status sv_expval_pauli(sv_handle h, uint64_t x, uint64_t z, double *out) {
+    SV_API_BEGIN
+    if (!h || !out) fail(SV_ERR_ARG, "null argument");
+    if ((x >> h->n) || (z >> h->n)) fail(SV_ERR_ARG, "Pauli mask outside the register");
+    const int nb = reduce_blocks(h->n);
+    ensure_scratch(h, (size_t)nb * 2 * sizeof(double));
+    launch_partial_expval(h->dtype, h->amp, h->n, x, z, h->scratch, nb, h->stream);
+    std::vector<double> part((size_t)nb * 2);
+    check_cuda(cudaMemcpyAsync(part.data(), h->scratch, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync(partials)");
+    check_dev_error(h);
+    double sr = 0, si = 0;
+    for (int b = 0; b < nb; ++b) {
+        sr += part[2 * b];
+        si += part[2 * b + 1];
+    }
+    // multiply by i^{popc(x & z)}
+    switch (__builtin_popcountll(x & z) & 3) {
+        case 1: { double t = sr; sr = -si; si = t; break; }
+        case 2: sr = -sr; si = -si; break;
+        case 3: { double t = sr; sr = si; si = -t; break; }
+        default: break;
+    }
+    out[0] = sr;
+    out[1] = si;
+    SV_API_END
+}
+
+sv_status sv_sample(sv_handle h, int64_t shots, uint64_t seed, uint64_t *out) {
+    SV_API_BEGIN
+    if (!h || (shots > 0 && !out)) fail(SV_ERR_ARG, "null argument");
+    if (shots < 0) fail(SV_ERR_ARG, "negative shot count");
+    if (shots == 0) return SV_OK;
+    const int sb = std::min(h->n, 10);
+    const int64_t nb = int64_t(1) << (h->n - sb);
+    // scratch: range sums, then per-shot (prefix, range, target) and results
+    const size_t need = (size_t)nb * sizeof(double) + (size_t)shots * (sizeof(double) * 2 + sizeof(int64_t) + sizeof(uint64_t)) + 1024;
+    ensure_scratch(h, need);
+    double *sums = h->scratch;
+    launch_block_sums(h->dtype, h->amp, h->n, sb, sums, h->stream);
+    std::vector<double> incl((size_t)nb);
+    check_cuda(cudaMemcpyAsync(incl.data(), sums, nb * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync(range sums)");
+    check_dev_error(h);
+    double acc = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        acc += incl[(size_t)b];
+        incl[(size_t)b] = acc;
+    }
+    const double total = acc;
+    if (!(total > 0)) fail(SV_ERR_ARG, "state has zero norm");
+    std::vector<double> prefix((size_t)shots), target((size_t)shots);
+    std::vector<int64_t> blk((size_t)shots);
+    for (int64_t s = 0; s < shots; ++s) {
+        const double t = splitmix_uniform(seed, (uint64_t)s) * total;
+        // smallest range whose inclusive prefix exceeds t
+        int64_t lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (incl[(size_t)mid] > t) hi = mid; else lo = mid + 1;
+        }
+        blk[(size_t)s] = lo;
+        prefix[(size_t)s] = lo > 0 ? incl[(size_t)lo - 1] : 0.0;
+        target[(size_t)s] = t;
+    }
+    unsigned char *p = reinterpret_cast<unsigned char *>(h->scratch) + (((size_t)nb * sizeof(double) + 255) / 256) * 256;
+    double *d_prefix = reinterpret_cast<double *>(p);
+    double *d_target = d_prefix + shots;
+    int64_t *d_blk = reinterpret_cast<int64_t *>(d_target + shots);
+    uint64_t *d_out = reinterpret_cast<uint64_t *>(d_blk + shots);
+    check_cuda(cudaMemcpyAsync(d_prefix, prefix.data(), shots * sizeof(double), cudaMemcpyHostToDevice, h->stream), "H2D");
+    check_cuda(cudaMemcpyAsync(d_target, target.data(), shots * sizeof(double), cudaMemcpyHostToDevice, h->stream), "H2D");
+    check_cuda(cudaMemcpyAsync(d_blk, blk.data(), shots * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream), "H2D");
+    launch_sample_within(h->dtype, h->amp, h->n, sb, d_prefix, d_blk, d_target, shots, d_out, h->stream);
+    check_cuda(cudaMemcpyAsync(out, d_out, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream), "D2H");
+    check_dev_error(h);
+    SV_API_END
+}
+
+}  // extern "C"

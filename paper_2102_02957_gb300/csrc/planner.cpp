@@ -1,0 +1,315 @@
+// Cache-blocking transpiler (host) -- Sec. IV.A of Doi & Horii (Listing 3) and the output
+// reordering of Sec. IV.C (Fig. 10 case (b)).
+//
+// Readings of the points the paper leaves open (the same readings the oracle takes):
+//  * QB_CHUNK holds c - reserve qubits ("QB_CHUNK[nc-1]" read as nc entries when reserve = 0).
+//  * Choice order: the first remaining gate's qubits (guarantees progress), then qubits of
+//    multi-qubit gates in list order, then of 1-qubit gates, then already-resident qubits by
+//    ascending physical bit; a gate whose new qubits do not all fit is skipped (all qubits of
+//    a multi-qubit gate enter the chunk together, Sec. IV.A).
+//  * A chunk_swap round pairs the incoming qubits (sorted by id) with the vacated chunk bits
+//    (sorted ascending); each pair swaps physical bits (slot < c, old position >= c).
+//  * The listing's "set QB_CHUNK" in the deferral branch is read as setting QB_BLOCKED: a
+//    deferred gate with any qubit in the chunk blocks all of its qubits.
+//  * SWAP gates are relabels; the final reordering is a bit permutation split into two rounds
+//    of disjoint transpositions.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o) {
+    if (n < 1 || n > 62) fail(SV_ERR_ARG, "n out of range");
+    if (n_gates < 0 || (n_gates > 0 && !gates)) fail(SV_ERR_ARG, "null gate list");
+    const int c = o.chunk_bits;
+    if (c < 1) fail(SV_ERR_ARG, "chunk_bits must be >= 1");
+    if (o.reserve != 0 && o.reserve != 1) fail(SV_ERR_ARG, "reserve must be 0 or 1");
+    const int width = std::min(c, n);
+    const int target = std::min(c - o.reserve, n);
+    if (target < 1) fail(SV_ERR_ARG, "chunk too small");
+
+    struct PG {
+        int64_t gi;
+        int32_t nq;
+        int32_t lq[2];  // labels in the gate's own order
+        int32_t vq[2];  // virtual qubits
+        uint64_t vmask;
+    };
+
+    auto *plan = new sv_plan();
+    plan->n = n;
+    plan->c = c;
+    plan->reserve = o.reserve;
+    plan->restore = o.restore_layout ? 1 : 0;
+    plan->seg_bits = SEG_BITS;
+    plan->use_tc = o.use_tc;
+    plan->keys.reserve((size_t)n_gates);
+
+    std::vector<int32_t> lab(n);
+    std::iota(lab.begin(), lab.end(), 0);
+    std::vector<PG> remaining;
+    remaining.reserve((size_t)n_gates);
+    for (int64_t i = 0; i < n_gates; ++i) {
+        const sv_gate &g = gates[i];
+        if (g.nq != 1 && g.nq != 2) { delete plan; fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": nq must be 1 or 2"); }
+        for (int j = 0; j < g.nq; ++j)
+            if (g.q[j] < 0 || g.q[j] >= n) { delete plan; fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range"); }
+        if (g.nq == 2 && g.q[0] == g.q[1]) { delete plan; fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit"); }
+        plan->keys.push_back(GateKey{g.nq, g.q[0], g.nq == 2 ? g.q[1] : -1, g.flags});
+        if (g.flags & SV_GATE_SWAP) {
+            if (g.nq != 2) { delete plan; fail(SV_ERR_ARG, "SWAP gate needs 2 qubits"); }
+            std::swap(lab[g.q[0]], lab[g.q[1]]);
+            continue;
+        }
+        if (g.nq > target) { delete plan; fail(SV_ERR_ARG, "gate " + std::to_string(i) + " is wider than the chunk"); }
+        PG p{};
+        p.gi = i;
+        p.nq = g.nq;
+        p.vmask = 0;
+        for (int j = 0; j < g.nq; ++j) {
+            p.lq[j] = g.q[j];
+            p.vq[j] = lab[g.q[j]];
+            p.vmask |= 1ull << p.vq[j];
+        }
+        remaining.push_back(p);
+    }
+
+    std::vector<int32_t> m(n), pinv(n);
+    std::iota(m.begin(), m.end(), 0);
+    std::iota(pinv.begin(), pinv.end(), 0);
+
+    std::vector<PG> next;
+    while (!remaining.empty()) {
+        // choose QB_CHUNK
+        uint64_t chosen = 0;
+        int cnt = 0;
+        auto try_add = [&](uint64_t msk) {
+            const uint64_t fresh = msk & ~chosen;
+            if (cnt + popc(fresh) <= target) {
+                chosen |= fresh;
+                cnt += popc(fresh);
+            }
+        };
+        try_add(remaining.front().vmask);
+        for (const PG &g : remaining) {
+            if (cnt >= target) break;
+            if (g.nq > 1) try_add(g.vmask);
+        }
+        for (const PG &g : remaining) {
+            if (cnt >= target) break;
+            if (g.nq == 1) try_add(g.vmask);
+        }
+        for (int p = 0; p < width && cnt < target; ++p) try_add(1ull << pinv[p]);
+
+        // chunk_swap round
+        PlanOp round;
+        round.kind = 1;
+        std::vector<int32_t> incoming, vacated;
+        for (int v = 0; v < n; ++v)
+            if (((chosen >> v) & 1) && m[v] >= width) incoming.push_back(v);
+        for (int p = 0; p < width; ++p)
+            if (!((chosen >> pinv[p]) & 1)) vacated.push_back(p);
+        for (size_t k = 0; k < incoming.size(); ++k) {
+            const int v_in = incoming[k], slot = vacated[k];
+            const int old = m[v_in], v_out = pinv[slot];
+            m[v_in] = slot;
+            pinv[slot] = v_in;
+            m[v_out] = old;
+            pinv[old] = v_out;
+            round.pairs.emplace_back(slot, old);
+        }
+        if (!round.pairs.empty()) plan->ops.push_back(std::move(round));
+
+        // scan REMAINING with QB_BLOCKED
+        PlanOp block;
+        block.kind = 2;
+        uint64_t blocked = 0;
+        next.clear();
+        for (const PG &g : remaining) {
+            if ((g.vmask & ~chosen) == 0 && (g.vmask & blocked) == 0) {
+                BlockGate bg{};
+                bg.gi = g.gi;
+                bg.nq = g.nq;
+                for (int j = 0; j < g.nq; ++j) {
+                    bg.phys[j] = m[g.vq[j]];
+                    bg.label[j] = g.lq[j];
+                }
+                if (g.nq == 1) { bg.phys[1] = -1; bg.label[1] = -1; }
+                block.gates.push_back(bg);
+            } else {
+                next.push_back(g);
+                if (g.vmask & chosen) blocked |= g.vmask;
+            }
+        }
+        plan->ops.push_back(std::move(block));
+        remaining.swap(next);
+    }
+
+    // output reordering: bit src[q] = m[lab[q]] must move to bit q
+    std::vector<int32_t> src(n);
+    for (int q = 0; q < n; ++q) src[q] = m[lab[q]];
+    if (plan->restore) {
+        std::vector<int32_t> dest(n);
+        for (int q = 0; q < n; ++q) dest[src[q]] = q;
+        PlanOp r1, r2;
+        r1.kind = r2.kind = 3;
+        std::vector<char> seen(n, 0);
+        for (int x0 = 0; x0 < n; ++x0) {
+            if (seen[x0]) continue;
+            std::vector<int32_t> cyc{x0};
+            seen[x0] = 1;
+            for (int y = dest[x0]; y != x0; y = dest[y]) {
+                cyc.push_back(y);
+                seen[y] = 1;
+            }
+            const int L = (int)cyc.size();
+            if (L == 1) continue;
+            for (int i = 1; i <= (L - 1) / 2; ++i) {
+                int a = cyc[i], b = cyc[L - i];
+                r1.pairs.emplace_back(std::min(a, b), std::max(a, b));
+            }
+            for (int i = 1; i <= L / 2; ++i) {
+                int a = cyc[i], b = cyc[(L + 1 - i) % L];
+                r2.pairs.emplace_back(std::min(a, b), std::max(a, b));
+            }
+        }
+        for (PlanOp *r : {&r1, &r2}) {
+            if (r->pairs.empty()) continue;
+            std::sort(r->pairs.begin(), r->pairs.end());
+            plan->ops.push_back(std::move(*r));
+        }
+        plan->final_map.resize(n);
+        std::iota(plan->final_map.begin(), plan->final_map.end(), 0);
+    } else {
+        plan->final_map = src;
+    }
+
+    // register groups per block (for statistics and execution)
+    int nseg = 0;
+    for (const PlanOp &op : plan->ops)
+        if (op.kind == 2) nseg += (int)segment_block(op.gates, std::min(c, n)).size();
+    plan->n_segments = nseg;
+    return plan;
+}
+
+// ---------------------------------------------------------------------------------------
+// Register groups.  Inside a blocking section each chunk lives in shared memory; a group is
+// a set of SEG_BITS chunk bits whose 2^SEG_BITS amplitudes one thread holds in registers
+// while it applies every gate of the group.  Gates are taken greedily in block order; a gate
+// that does not fit is deferred and blocks its bits for the rest of the group (so per-qubit
+// gate order is kept), the same rule the transpiler uses one level up.
+std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width) {
+    std::vector<HostSeg> segs;
+    std::vector<int32_t> pending(gates.size());
+    std::iota(pending.begin(), pending.end(), 0);
+    auto mask_of = [&](const BlockGate &g) {
+        uint64_t mk = 1ull << g.phys[0];
+        if (g.nq == 2) mk |= 1ull << g.phys[1];
+        return mk;
+    };
+    std::vector<int32_t> rest;
+    while (!pending.empty()) {
+        uint64_t set = 0, blocked = 0;
+        HostSeg s{};
+        rest.clear();
+        for (int32_t idx : pending) {
+            const uint64_t mk = mask_of(gates[idx]);
+            if ((mk & blocked) == 0 && popc(set | mk) <= SEG_BITS) {
+                set |= mk;
+                s.gates.push_back(idx);
+            } else {
+                blocked |= mk;
+                rest.push_back(idx);
+            }
+        }
+        // pad with the highest unused chunk bits (keeps the low bits spread across lanes)
+        for (int p = width - 1; p >= 0 && popc(set) < SEG_BITS; --p)
+            if (!((set >> p) & 1)) set |= 1ull << p;
+        int k = 0;
+        for (int p = 0; p < 64 && k < SEG_BITS; ++p)
+            if ((set >> p) & 1) s.pos[k++] = p;
+        segs.push_back(std::move(s));
+        pending.swap(rest);
+    }
+    return segs;
+}
+
+template <typename T>
+void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevGate<T> &out) {
+    auto local = [&](int phys) {
+        for (int k = 0; k < SEG_BITS; ++k)
+            if (seg.pos[k] == phys) return k;
+        fail(SV_ERR_PLAN, "gate bit outside its register group");
+    };
+    std::memset(&out, 0, sizeof(out));
+    if (g.nq == 1) {
+        out.a = local(bg.phys[0]);
+        out.b = -1;
+        out.code = out.a;
+        const bool diag = g.m[2] == 0.0 && g.m[3] == 0.0 && g.m[4] == 0.0 && g.m[5] == 0.0;
+        if (diag) {
+            out.op = OP_DIAG1;
+            out.m[0] = (T)g.m[0]; out.m[1] = (T)g.m[1];
+            out.m[2] = (T)g.m[6]; out.m[3] = (T)g.m[7];
+        } else {
+            out.op = OP_DENSE1;
+            for (int i = 0; i < 8; ++i) out.m[i] = (T)g.m[i];
+        }
+        return;
+    }
+    int la = local(bg.phys[0]), lb = local(bg.phys[1]);
+    // matrix in local basis bit(la) + 2*bit(lb); reorder so that the lower register bit is
+    // the low local bit.
+    double mm[32];
+    if (la < lb) {
+        std::memcpy(mm, g.m, sizeof(mm));
+    } else {
+        auto sw = [](int i) { return ((i & 1) << 1) | ((i >> 1) & 1); };
+        for (int r = 0; r < 4; ++r)
+            for (int cc = 0; cc < 4; ++cc) {
+                mm[2 * (r * 4 + cc)] = g.m[2 * (sw(r) * 4 + sw(cc))];
+                mm[2 * (r * 4 + cc) + 1] = g.m[2 * (sw(r) * 4 + sw(cc)) + 1];
+            }
+        std::swap(la, lb);
+    }
+    out.a = la;
+    out.b = lb;
+    out.code = la * SEG_BITS + lb;
+    bool diag = true, perm = true;
+    for (int r = 0; r < 4; ++r) {
+        int ones = 0;
+        for (int cc = 0; cc < 4; ++cc) {
+            const double re = mm[2 * (r * 4 + cc)], im = mm[2 * (r * 4 + cc) + 1];
+            if (r != cc && (re != 0.0 || im != 0.0)) diag = false;
+            if (re == 1.0 && im == 0.0) ++ones;
+            else if (re != 0.0 || im != 0.0) perm = false;
+        }
+        if (ones != 1) perm = false;
+    }
+    if (diag) {
+        out.op = OP_DIAG2;
+        for (int r = 0; r < 4; ++r) {
+            out.m[2 * r] = (T)mm[2 * (r * 4 + r)];
+            out.m[2 * r + 1] = (T)mm[2 * (r * 4 + r) + 1];
+        }
+    } else if (perm) {
+        out.op = OP_PERM2;
+        // m[r] = source column of output row r
+        for (int r = 0; r < 4; ++r)
+            for (int cc = 0; cc < 4; ++cc)
+                if (mm[2 * (r * 4 + cc)] == 1.0) out.m[r] = (T)cc;
+    } else {
+        out.op = OP_DENSE2;
+        for (int i = 0; i < 32; ++i) out.m[i] = (T)mm[i];
+    }
+}
+
+template void encode_gate<float>(const sv_gate &, const BlockGate &, const HostSeg &, DevGate<float> &);
+template void encode_gate<double>(const sv_gate &, const BlockGate &, const HostSeg &, DevGate<double> &);
+
+}  // namespace sv

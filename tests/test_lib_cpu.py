@@ -1,0 +1,115 @@
+"""Host-side checks of the CUDA library without a GPU: it loads, exports every entry point that
+include/sv.h declares, builds gate matrices like the oracle, and its planner's schedules match
+the oracle planner bit for bit.  No kernel is launched here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from oracle import gates as og
+from oracle import planner
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sv():
+    from paper_2102_02957_gb300 import build
+    build.build()
+    import paper_2102_02957_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(sv_[a-z0-9_]+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(sv):
+    declared = _declared_functions()
+    assert len(declared) >= 20
+    lib = sv.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(sv):
+    declared = set(_declared_functions())
+    bound = set(sv._lib.exported_names())
+    assert declared == bound, (declared - bound, bound - declared)
+
+
+KINDS = [("u3", (3,), (0.3, 1.1, -2.0)), ("h", (1,), ()), ("x", (0,), ()), ("y", (2,), ()), ("z", (3,), ()),
+         ("ry", (1,), (0.7,)), ("rz", (2,), (1.9,)), ("cx", (3, 1), ()), ("cz", (0, 2), ()),
+         ("cp", (1, 3), (0.45,)), ("swap", (0, 3), ())]
+
+
+@pytest.mark.parametrize("desc", KINDS)
+def test_gate_matrices_match_oracle(sv, desc):
+    kind, qubits, params = desc
+    rec = sv.make_gates([desc])[0]
+    order, m = og.matrix_of(kind, qubits, params)
+    nq = len(order)
+    assert rec["nq"] == nq and tuple(rec["q"][:nq]) == tuple(order)
+    got = rec["m"][: 2 * (1 << nq) ** 2].view(np.complex128).reshape(1 << nq, 1 << nq)
+    assert np.abs(got - m).max() < 1e-15
+    assert bool(rec["flags"] & sv.SV_GATE_SWAP) == (kind == "swap")
+
+
+def test_unitary_gate_roundtrip(sv):
+    rng = np.random.Generator(np.random.PCG64(1))
+    u = cg.haar_unitary(rng)
+    rec = sv.make_gates([("unitary", (4, 2), (u,))])[0]
+    assert tuple(rec["q"]) == (4, 2)
+    assert np.array_equal(rec["m"].view(np.complex128).reshape(4, 4), u)
+
+
+def _circuits(n, seed):
+    return [cg.random_layers(n, 4, seed), cg.quantum_volume(n, 4, seed), cg.qft(n), cg.hea(n, 2, seed, 1),
+            cg.noisy_trajectory(n, 3, 0.3, seed, 2), cg.mirror(cg.quantum_volume(n, 2, seed + 1))]
+
+
+@pytest.mark.parametrize("n", [4, 7, 12, 16, 30])
+@pytest.mark.parametrize("c", [2, 4, 6, 10, 13])
+def test_planner_schedule_parity(sv, n, c):
+    for reserve in (0, 1):
+        if c - reserve < 2:
+            continue
+        for restore in (True, False):
+            for desc in _circuits(n, 3 * n + c):
+                gates = sv.make_gates(desc)
+                p = sv.Plan(n, gates, chunk_bits=c, reserve=reserve, restore_layout=restore)
+                q = planner.plan_blocking(n, desc, c, reserve, restore)
+                assert p.serialize() == q.serialize()
+                inf = p.info()
+                assert inf.n_blocks == q.n_blocks and inf.n_swap_rounds == q.n_swap_rounds
+                assert list(inf.final_map[:n]) == q.final_map
+
+
+def test_planner_full_size_workloads(sv):
+    for name in ("qv30", "rl28", "qft28", "rl16", "qv32"):
+        w = cg.WORKLOADS[name]
+        desc = cg.build(name)
+        p = sv.Plan(w["n"], sv.make_gates(desc), chunk_bits=w["c"])
+        q = planner.plan_blocking(w["n"], desc, w["c"])
+        assert p.serialize() == q.serialize(), name
+
+
+def test_planner_errors(sv):
+    gates = sv.make_gates([("cx", (0, 1), ())])
+    with pytest.raises(sv.SVError) as e:
+        sv.Plan(4, gates, chunk_bits=2, reserve=1)
+    assert e.value.status == sv._lib.SV_ERR_ARG
+    bad = gates.copy()
+    bad[0]["q"][0] = 9
+    with pytest.raises(sv.SVError):
+        sv.Plan(4, bad, chunk_bits=3)
+    with pytest.raises(sv.SVError):
+        sv.make_gates([("cx", (1, 1), ())])
