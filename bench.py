@@ -222,6 +222,31 @@ def _traffic_for(kernel_src: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def _per_gate(sv, st, desc, stream, args, sweep_bytes):
+    import torch
+    G = len(desc)
+    gates = sv.make_gates(desc)
+    st.init_basis(0)
+    st.apply(gates)
+    st.synchronize()
+    pg_steps = max(1, min(2, args.steps))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pg_steps):
+        st.init_basis(0)
+        st.apply(gates)
+        st.norm2()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pg_ms = e0.elapsed_time(e1) / pg_steps
+    s = st.stats()
+    per_gate = {"gates_per_s": G / (pg_ms / 1000.0), "ms_per_step": pg_ms,
+                "effective_GBs": G * sweep_bytes / (pg_ms / 1000.0) / 1e9,
+                "kernel_GBs": G * sweep_bytes / (s.ms_gate / 1000.0) / 1e9 if s.ms_gate else None}
+    return per_gate, pg_ms
+
+
 # ------------------------------------------------------------------ main GPU benchmark
 def run_ours(args):
     import numpy as np
@@ -305,25 +330,10 @@ def run_ours(args):
                               "GBs": perm_gbs, "share": ms_perm / (ms_block + ms_perm)}}
 
     # plain per-gate GPU path on the same workload (the paper's baseline)
-    gates = sv.make_gates(desc)
-    st.init_basis(0)
-    st.apply(gates)
-    st.synchronize()
-    pg_steps = max(1, min(2, args.steps))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(pg_steps):
-        st.init_basis(0)
-        st.apply(gates)
-        st.norm2()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    pg_ms = e0.elapsed_time(e1) / pg_steps
-    s = st.stats()
-    per_gate = {"gates_per_s": G / (pg_ms / 1000.0), "ms_per_step": pg_ms,
-                "effective_GBs": G * sweep_bytes / (pg_ms / 1000.0) / 1e9,
-                "kernel_GBs": G * sweep_bytes / (s.ms_gate / 1000.0) / 1e9 if s.ms_gate else None}
+    per_gate = None
+    pg_ms = float("nan")
+    if not args.no_per_gate:
+        per_gate, pg_ms = _per_gate(sv, st, desc, stream, args, sweep_bytes)
 
     # end to end through the C ABI with host buffers: H2D of the input state, plan, apply,
     # D2H of the output state
@@ -374,7 +384,7 @@ def run_ours(args):
             "effective_hbm_GBs": eff_gbs, "effective_hbm_frac": eff_gbs / peak,
             "sweeps_per_step": {"blocks": info.n_blocks, "swap_rounds": info.n_swap_rounds,
                                 "reorder_rounds": info.n_unpermute_rounds},
-            "per_gate": per_gate, "speedup_vs_per_gate": pg_ms / ms_step,
+            "per_gate": per_gate, "speedup_vs_per_gate": (pg_ms / ms_step) if per_gate else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": launches, "norm": norm_last,
         }
@@ -392,6 +402,7 @@ def main():
     ap.add_argument("--workload", default="qv30")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()

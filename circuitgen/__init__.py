@@ -187,6 +187,7 @@ WORKLOADS = {
     "qft28": dict(kind="qft", n=28, seed=2, c=12),
     "rl28": dict(kind="random_layers", n=28, depth=40, seed=3, c=12),
     "qv30": dict(kind="quantum_volume", n=30, depth=30, seed=4, c=13),
+    "qv26": dict(kind="quantum_volume", n=26, depth=10, seed=4, c=13),
     "rl32": dict(kind="random_layers", n=32, depth=32, seed=7, c=13),
     "qv32": dict(kind="quantum_volume", n=32, depth=32, seed=7, c=13),
 }
