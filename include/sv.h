@@ -184,6 +184,21 @@ sv_status sv_sample(sv_handle h, int64_t shots, uint64_t seed, uint64_t *out);
  * out[0] = real part, out[1] = imaginary part (host). */
 sv_status sv_expval_pauli(sv_handle h, uint64_t x_mask, uint64_t z_mask, double *out);
 
+/* The same value as sv_expval_pauli, for callers that must not allocate memory at the time of
+ * the call (a memory budget or pool they do not own, or loops where a cudaMalloc/cudaFree would
+ * stall the device).  The paper has no counterpart; this is a service of this library.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its partial sums go to a fixed
+ * 64 KiB array compiled into the library (4096 (re, im) pairs plus the result), which every GPU
+ * that loads the library holds until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current, so make that
+ * first call before any stream capture.  The handle's device must be the current device
+ * (SV_ERR_ARG otherwise).  A state that would need more than 4096 partial sums (more than 512
+ * SMs) is rejected with SV_ERR_UNSUPPORTED.  All calls share the array and it keeps the last
+ * call's contents: calls whose kernels overlap on the GPU (different streams, threads) race
+ * and must be serialised by the caller.  Synchronises the handle's stream; out[0] = real part,
+ * out[1] = imaginary part (host). */
+sv_status sv_expval_pauli_noalloc(sv_handle h, uint64_t x_mask, uint64_t z_mask, double *out);
+
 /* Thread-local message for the last failed call on this thread ("" if none). */
 const char *sv_last_error(void);
 

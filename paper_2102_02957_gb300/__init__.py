@@ -162,6 +162,12 @@ class StateVector:
         check(lib().sv_expval_pauli(self._h, x_mask, z_mask, v))
         return complex(v[0], v[1])
 
+    def expval_pauli_noalloc(self, x_mask: int, z_mask: int) -> complex:
+        """sv_expval_pauli_noalloc: same value, partial sums in the library's fixed scratch."""
+        v = (ctypes.c_double * 2)()
+        check(lib().sv_expval_pauli_noalloc(self._h, x_mask, z_mask, v))
+        return complex(v[0], v[1])
+
     def close(self):
         if self._h:
             lib().sv_destroy(self._h)

@@ -76,6 +76,7 @@ _SIGS = {
     "sv_sample": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint64, _VP]),
     "sv_expval_pauli": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "sv_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "sv_expval_pauli_noalloc": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "sv_last_error": (ctypes.c_char_p, []),
 }
 
