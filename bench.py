@@ -262,6 +262,8 @@ def run_ours(args):
     import paper_2102_02957_gb300 as sv
 
     w = _workload(args.workload)
+    if args.chunk_bits:
+        w["c"] = args.chunk_bits
     n, c, desc = w["n"], w["c"], w["desc"]
     G = len(desc)
     stream = torch.cuda.Stream()
@@ -271,7 +273,7 @@ def run_ours(args):
 
     def step():
         gates = sv.make_gates(desc)
-        plan = sv.Plan(n, gates, chunk_bits=c)
+        plan = sv.Plan(n, gates, chunk_bits=c, seg_bits=args.seg_bits)
         st.init_basis(0)
         st.apply(gates, plan)
         nrm = st.norm2()
@@ -403,6 +405,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
+    ap.add_argument("--seg-bits", type=int, default=5, help="register-group width inside a chunk (4 or 5)")
+    ap.add_argument("--chunk-bits", type=int, default=0, help="override the workload's chunk bits")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()

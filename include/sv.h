@@ -80,7 +80,11 @@ typedef struct sv_options {
     int32_t use_tc;         /* 1: apply fused groups as 3xTF32 tensor-core contractions (complex64) */
     int32_t use_model;      /* 1: let a trained cost model steer QB_CHUNK choices (sv_costmodel_*) */
     int32_t threads;        /* consumer threads per chunk CTA; 0 = auto                             */
-    int32_t reserved[9];
+    int32_t gather_pinned;  /* 0: the paper's chunk_swap rounds make every chunk bits 0..c-1.  p > 0:
+                               gathered chunks -- a chunk is the low p bits plus c-p chosen bits,
+                               fetched in place (no chunk_swap passes, no data reordering); the
+                               transpiler's choice rule starts from the p pinned bits.  default 0 */
+    int32_t reserved[8];
 } sv_options;
 
 void sv_options_default(sv_options *opts);
@@ -135,7 +139,8 @@ sv_status sv_plan_get_info(sv_plan_h plan, sv_plan_info *info);
  *   [1, r, (p, q) x r]                 chunk_swap round (p < c <= q)
  *   [2, G, (gate_index, nq, p0, p1) x G]  block; p0/p1 = physical bits of the gate's qubits in
  *                                         ascending logical order, p1 = -1 for 1 qubit
- *   [3, r, (p, q) x r]                 output-reordering round.
+ *   [3, r, (p, q) x r]                 output-reordering round
+ *   [4, mask, G, (gate_index, nq, p0, p1) x G]  gathered block over the chunk bits in `mask`.
  * Writes at most `cap` values to buf; *len receives the full length (call with cap 0 to
  * size the buffer). */
 sv_status sv_plan_serialize(sv_plan_h plan, int64_t *buf, int64_t cap, int64_t *len);

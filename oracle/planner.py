@@ -31,6 +31,12 @@ physical bit q holds logical qubit q (Sec. IV.C: "reorder qubits for the output"
 (b)).  That reordering is a bit permutation, written as two rounds of disjoint transpositions:
 for each cycle x0 -> x1 -> ... (x0 its smallest bit, x_{i+1} = destination of x_i) the first
 round exchanges x_i <-> x_{L-i} and the second x_i <-> x_{L+1-i} (indices mod L).
+
+Gathered chunks (``pinned > 0``): the same loop without data movement.  A chunk is any set of c
+bits that contains the low ``pinned`` bits; the section gathers it from HBM instead of having
+chunk_swap rounds make it contiguous.  QB_CHUNK starts as the pinned qubits and is filled by the
+same priority rule; no swap round is emitted and the map stays the identity, so only SWAP
+relabels can leave an output reordering.  Each section is ("gblock", chunk_mask, gates).
 """
 from __future__ import annotations
 
@@ -44,7 +50,9 @@ class Plan:
     reserve: int
     restore_layout: bool
     ops: list = field(default_factory=list)  # ("swap"|"unpermute", [(p, q)]) / ("block", [(gi, phys)])
+    #                                          / ("gblock", (chunk_mask, [(gi, phys)]))
     final_map: list = field(default_factory=list)  # physical bit of each logical qubit at the end
+    pinned: int = 0
 
     def serialize(self):
         """Integer stream used to compare schedules bit for bit with the library's planner."""
@@ -55,15 +63,30 @@ class Plan:
                 for p, q in body:
                     out += [p, q]
             else:
-                out += [2, len(body)]
+                if kind == "gblock":
+                    mask, body = body
+                    out += [4, mask, len(body)]
+                else:
+                    out += [2, len(body)]
                 for gi, phys in body:
                     out += [gi, len(phys), phys[0], phys[1] if len(phys) > 1 else -1]
         out += list(self.final_map)
         return out
 
+    def blocks(self):
+        """(chunk bits, gate list) of every section; a contiguous chunk is bits 0..c-1."""
+        out = []
+        for kind, body in self.ops:
+            if kind == "block":
+                out.append((list(range(min(self.c, self.n))), body))
+            elif kind == "gblock":
+                mask, gl = body
+                out.append(([b for b in range(self.n) if (mask >> b) & 1], gl))
+        return out
+
     @property
     def n_blocks(self):
-        return sum(1 for k, _ in self.ops if k == "block")
+        return sum(1 for k, _ in self.ops if k in ("block", "gblock"))
 
     @property
     def n_swap_rounds(self):
@@ -80,7 +103,7 @@ def _canonical_qubits(kind, qubits):
     return tuple(sorted(qubits))
 
 
-def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True) -> Plan:
+def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True, pinned: int = 0) -> Plan:
     if not (1 <= n <= 62):
         raise ValueError("n out of range")
     if c < 1:
@@ -91,6 +114,8 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
     target = min(c - reserve, n)
     if target < 1:
         raise ValueError("chunk too small")
+    if pinned < 0 or pinned > n or (pinned and target - pinned < 2):
+        raise ValueError("pinned bits leave no room for a 2-qubit gate")
 
     # SWAP gates as relabels: lab[label] = virtual qubit carrying that label.
     lab = list(range(n))
@@ -112,7 +137,7 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
 
     m = list(range(n))  # virtual (logical) qubit -> physical bit
     pinv = list(range(n))  # physical bit -> virtual qubit
-    plan = Plan(n=n, c=c, reserve=reserve, restore_layout=restore_layout)
+    plan = Plan(n=n, c=c, reserve=reserve, restore_layout=restore_layout, pinned=pinned)
 
     while remaining:
         # -- choose QB_CHUNK
@@ -128,6 +153,8 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
                 chosen.extend(new)
                 chosen_set.update(new)
 
+        for p in range(pinned):  # gathered chunks always hold the low `pinned` bits
+            try_add((pinv[p],))
         try_add(remaining[0][1])
         for _gi, qs in remaining:
             if len(chosen) >= target:
@@ -139,13 +166,13 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
                 break
             if len(qs) == 1:
                 try_add(qs)
-        for p in range(width):
+        for p in range(n if pinned else width):
             if len(chosen) >= target:
                 break
             try_add((pinv[p],))
 
-        # -- chunk_swap round
-        incoming = sorted(q for q in chosen if m[q] >= width)
+        # -- chunk_swap round (none for gathered chunks: the section gathers its bits)
+        incoming = [] if pinned else sorted(q for q in chosen if m[q] >= width)
         vacated = sorted(p for p in range(width) if pinv[p] not in chosen_set)
         pairs = []
         for q_in, slot in zip(incoming, vacated):
@@ -168,7 +195,13 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
                 nxt.append((gi, qs))
                 if any(q in chosen_set for q in qs):
                     blocked.update(qs)
-        plan.ops.append(("block", block))
+        if pinned:
+            mask = 0
+            for q in chosen:
+                mask |= 1 << m[q]
+            plan.ops.append(("gblock", (mask, block)))
+        else:
+            plan.ops.append(("block", block))
         remaining = nxt
 
     # -- output reordering: physical bit m[lab[q]] must end at bit q.
@@ -228,6 +261,14 @@ def validate(plan: Plan, gates) -> None:
                 assert 0 <= p < q < n
                 assert p not in used and q not in used
                 used.update((p, q))
+        elif kind == "gblock":
+            mask, gl = body
+            assert len(gl) > 0, "empty block"
+            assert bin(mask).count("1") <= width and mask < (1 << n)
+            assert all((mask >> b) & 1 for b in range(plan.pinned)), "pinned bits missing"
+            for gi, phys in gl:
+                assert all((mask >> p) & 1 for p in phys), (phys, mask)
+                emitted.append(gi)
         else:
             assert len(body) > 0, "empty block"
             for gi, phys in body:

@@ -197,9 +197,10 @@ def execute_plan(n: int, gates, plan, basis: int = 0, state: np.ndarray | None =
         if op[0] in ("swap", "unpermute"):
             for p, q in op[1]:
                 swap_bits(st, n, p, q)
-        elif op[0] == "block":
+        elif op[0] in ("block", "gblock"):
+            body = op[1][1] if op[0] == "gblock" else op[1]
             phys = []
-            for gi, pq in op[1]:
+            for gi, pq in body:
                 kind, qubits, params = gates[gi]
                 order, u = _gates.matrix_of(kind, qubits, params)
                 # pq lists the physical positions of the gate's qubits in ascending label

@@ -68,50 +68,70 @@ static void validate_gates(int n, const sv_gate *gates, int64_t n_gates) {
     }
 }
 
-// Device program of one blocking section.
+// Device program of one blocking section: register groups, then gate records, laid out as
+// the kernel copies them into shared memory.
 struct BlockProg {
-    size_t seg_off, gate_off;
+    size_t off;
     int nseg, ngate;
+    GatherLayout lay;  // gathered sections only
 };
 
 template <typename T>
-static void build_programs(const sv_plan *plan, const sv_gate *gates, std::vector<unsigned char> &host,
+static void build_programs(const sv_plan *plan, const sv_gate *gates, int seg_bits, std::vector<unsigned char> &host,
                            std::vector<BlockProg> &progs) {
-    const int width = std::min(plan->c, plan->n);
     host.clear();
     progs.clear();
     auto align = [&](size_t a) {
         while (host.size() % a) host.push_back(0);
     };
-    for (const PlanOp &op : plan->ops) {
-        if (op.kind != 2) continue;
-        std::vector<HostSeg> segs = segment_block(op.gates, width);
+    for (const PlanOp &op0 : plan->ops) {
+        if (op0.kind != 2 && op0.kind != 4) continue;
+        int width = std::min(plan->c, plan->n);
+        BlockProg bp{};
+        PlanOp local;
+        const PlanOp *opp = &op0;
+        if (op0.kind == 4) {  // gate bits -> chunk-local bits of the gathered layout
+            bp.lay = gather_layout(op0.mask, plan->n, (int)(2 * sizeof(T)));
+            local = op0;
+            for (BlockGate &g : local.gates)
+                for (int j = 0; j < g.nq; ++j) g.phys[j] = bp.lay.local_of[g.phys[j]];
+            width = bp.lay.ce;
+            opp = &local;
+        }
+        const PlanOp &op = *opp;
+        std::vector<HostSeg> segs = segment_block(op.gates, width, seg_bits, (int)(2 * sizeof(T)));
         std::vector<DevSeg> dsegs;
         std::vector<DevGate<T>> dgates;
         for (const HostSeg &s : segs) {
-            DevSeg d{};
-            for (int k = 0; k < SEG_BITS; ++k) d.pos[k] = s.pos[k];
-            d.g0 = (int32_t)dgates.size();
+            DevSeg d;
+            std::memset(&d, 0, sizeof(d));
+            d.r = (int8_t)s.r;
+            for (int k = 0; k < s.r; ++k) d.pos[k] = (int8_t)s.pos[k];
+            for (int k = 0; k < 5; ++k) d.lane[k] = (int8_t)s.lane[k];
+            d.nrest = (int8_t)s.nrest;
+            for (int k = 0; k < s.nrest; ++k) d.rest[k] = (int8_t)s.rest[k];
+            d.flags = (int8_t)s.flags;
+            d.g0 = (int16_t)dgates.size();
             for (int32_t gi : s.gates) {
                 DevGate<T> dg;
                 const BlockGate &bg = op.gates[gi];
                 encode_gate<T>(gates[bg.gi], bg, s, dg);
                 dgates.push_back(dg);
             }
-            d.g1 = (int32_t)dgates.size();
+            if (dgates.size() > 32767) fail(SV_ERR_UNSUPPORTED, "too many gates in one blocking section");
+            d.g1 = (int16_t)dgates.size();
             dsegs.push_back(d);
         }
-        BlockProg bp{};
         align(256);
-        bp.seg_off = host.size();
+        bp.off = host.size();
         bp.nseg = (int)dsegs.size();
+        bp.ngate = (int)dgates.size();
         const unsigned char *p = reinterpret_cast<const unsigned char *>(dsegs.data());
         host.insert(host.end(), p, p + dsegs.size() * sizeof(DevSeg));
-        align(256);
-        bp.gate_off = host.size();
-        bp.ngate = (int)dgates.size();
+        align(16);
         p = reinterpret_cast<const unsigned char *>(dgates.data());
         host.insert(host.end(), p, p + dgates.size() * sizeof(DevGate<T>));
+        align(16);
         progs.push_back(bp);
     }
     align(256);
@@ -175,7 +195,7 @@ void sv_options_default(sv_options *o) {
     o->chunk_bits = 13;
     o->reserve = 0;
     o->restore_layout = 1;
-    o->seg_bits = SEG_BITS;
+    o->seg_bits = 5;
     o->use_tc = 0;
     o->use_model = 0;
     o->threads = 0;
@@ -289,7 +309,7 @@ sv_status sv_plan_get_info(sv_plan_h p, sv_plan_info *info) {
     info->restore_layout = p->restore;
     for (const PlanOp &op : p->ops) {
         if (op.kind == 1) ++info->n_swap_rounds;
-        if (op.kind == 2) { ++info->n_blocks; info->n_gates_emitted += (int64_t)op.gates.size(); }
+        if (op.kind == 2 || op.kind == 4) { ++info->n_blocks; info->n_gates_emitted += (int64_t)op.gates.size(); }
         if (op.kind == 3) ++info->n_unpermute_rounds;
     }
     info->n_segments = p->n_segments;
@@ -303,7 +323,8 @@ sv_status sv_plan_serialize(sv_plan_h p, int64_t *buf, int64_t cap, int64_t *len
     std::vector<int64_t> v{p->n, p->c, p->reserve, p->restore, (int64_t)p->ops.size()};
     for (const PlanOp &op : p->ops) {
         v.push_back(op.kind);
-        if (op.kind == 2) {
+        if (op.kind == 2 || op.kind == 4) {
+            if (op.kind == 4) v.push_back((int64_t)op.mask);
             v.push_back((int64_t)op.gates.size());
             for (const BlockGate &g : op.gates) {
                 v.push_back(g.gi);
@@ -384,17 +405,22 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         }
         std::vector<unsigned char> host;
         std::vector<BlockProg> progs;
-        if (h->dtype == SV_C64) build_programs<float>(plan, gates, host, progs);
-        else build_programs<double>(plan, gates, host, progs);
+        const int seg_bits = h->dtype == SV_C64 ? plan->seg_bits : 4;
+        if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
+        else build_programs<double>(plan, gates, seg_bits, host, progs);
         upload_program(h, host);
         size_t bi = 0;
         const unsigned char *base = static_cast<const unsigned char *>(h->prog);
         for (const PlanOp &op : plan->ops) {
-            if (op.kind == 2) {
+            if (op.kind == 2 || op.kind == 4) {
                 const BlockProg &bp = progs[bi++];
                 mark_begin(h, 1);
-                launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.seg_off, bp.nseg, base + bp.gate_off,
-                             bp.ngate, h->dev_err, 0, h->stream);
+                if (op.kind == 2)
+                    launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
+                                 seg_bits, h->stream);
+                else
+                    launch_block_gather(h->dtype, h->amp, h->n, bp.lay, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
+                                        seg_bits, h->stream);
                 mark_end(h);
                 ++st.sweeps_block;
             } else {

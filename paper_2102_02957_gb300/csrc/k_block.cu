@@ -8,15 +8,26 @@
 //  * warp 0, lane 0 is the producer: it streams the CTA's chunks j = blockIdx.x + t*gridDim.x
 //    into a ring of NBUF shared-memory buffers with 1-D bulk asynchronous copies (TMA engine)
 //    completing on "full" mbarriers;
-//  * the other NC threads are consumers: for each chunk they run the section's register
-//    groups -- each thread loads the 2^SEG_BITS amplitudes of a group (bits listed in the
-//    group) from shared memory into registers, applies all the group's gates there, and
-//    stores them back -- then one consumer writes the chunk back with a bulk copy and, once
-//    a write-back has finished reading shared memory, releases that buffer to the producer
-//    through an "empty" mbarrier (with a ring of >= 3 buffers the release of buffer t waits
-//    until chunk t+1 is written back, so the consumer never stalls on its own write-back).
+//  * the other NC threads are consumers.  For each chunk they run the section's register
+//    groups: each thread loads the 2^R amplitudes spanned by the group's R chunk bits from
+//    shared memory into registers, applies every gate of the group there, and stores them
+//    back.  Then one consumer writes the chunk back with a bulk copy and releases the buffer
+//    to the producer through an "empty" mbarrier once the write-back has read it.
+//
+// Shared-memory layout of a chunk while it is being worked on: amplitude i sits in slot
+// i ^ F(i), where F XORs a fixed non-zero pattern V[k] into the low slot bits for every set
+// bit k >= SB of i (SB = log2 of the amplitudes per 128-byte row).  The bulk copies move the
+// natural layout, so the first group reads and the last group writes unswizzled slots.  For
+// every group the host picks which chunk bits the lanes of a half-warp (quarter-warp for
+// complex128) enumerate so that their slots fall in distinct banks.
+//
 // Every wait is bounded (globaltimer); on expiry the kernel records DEV_ERR_TIMEOUT in the
 // error word and stops.
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "ptx.cuh"
 #include "sv_internal.h"
 
@@ -30,8 +41,9 @@ template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
 
-constexpr int R = SEG_BITS;
-constexpr int NA = 1 << R;  // amplitudes per register group
+// Swizzle patterns V[k] (see sv_internal.h); the host picks lane layouts from the same table.
+__constant__ int c_swz64[24] = {SV_SWZ64_LIST};
+__constant__ int c_swz128[24] = {SV_SWZ128_LIST};
 
 __device__ __forceinline__ int insert0(int x, int p) { return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1)); }
 
@@ -43,7 +55,7 @@ __device__ __forceinline__ void cmul_acc(T &yr, T &yi, T mr, T mi, T xr, T xi) {
     yi = fma(mi, xr, yi);
 }
 
-template <typename T, int A>
+template <typename T, int NA, int A>
 __device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
     const T m0r = m[0], m0i = m[1], m1r = m[2], m1i = m[3], m2r = m[4], m2i = m[5], m3r = m[6], m3i = m[7];
 #pragma unroll
@@ -60,7 +72,7 @@ __device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], const T *__res
     }
 }
 
-template <typename T, int A>
+template <typename T, int NA, int A>
 __device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
     const T d0r = m[0], d0i = m[1], d1r = m[2], d1i = m[3];
 #pragma unroll
@@ -72,7 +84,7 @@ __device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], const T *__rest
     }
 }
 
-template <typename T, int A, int B>
+template <typename T, int NA, int A, int B>
 __device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
     T mm[32];
 #pragma unroll
@@ -95,7 +107,7 @@ __device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], const T *__res
     }
 }
 
-template <typename T, int A, int B>
+template <typename T, int NA, int A, int B>
 __device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
     T d[8];
 #pragma unroll
@@ -110,7 +122,7 @@ __device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], const T *__rest
     }
 }
 
-template <typename T, int A, int B>
+template <typename T, int NA, int A, int B>
 __device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
     const int p0 = (int)m[0], p1 = (int)m[1], p2 = (int)m[2], p3 = (int)m[3];
 #pragma unroll
@@ -130,90 +142,158 @@ __device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], const T *__rest
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void apply_gate(const DevGate<T> *__restrict__ g, int op, int code, T (&r)[NA], T (&i)[NA]) {
-    const T *m = g->m;
-#define SV_1Q(A)                                   \
-    case A:                                        \
-        if (op == OP_DENSE1) ap_dense1<T, A>(r, i, m); \
-        else ap_diag1<T, A>(r, i, m);              \
-        break;
-#define SV_2Q(A, B)                                          \
-    case A * R + B:                                          \
-        if (op == OP_DENSE2) ap_dense2<T, A, B>(r, i, m);    \
-        else if (op == OP_DIAG2) ap_diag2<T, A, B>(r, i, m); \
-        else ap_perm2<T, A, B>(r, i, m);                     \
-        break;
+// Dispatch a gate on the register bits (a, b) -- compile-time bit positions via templates.
+template <typename T, int R, int A>
+__device__ __forceinline__ void one(int op, T (&r)[1 << R], T (&i)[1 << R], const T *m) {
+    if (op == OP_DENSE1) ap_dense1<T, 1 << R, A>(r, i, m);
+    else ap_diag1<T, 1 << R, A>(r, i, m);
+}
+
+template <typename T, int R, int A, int B>
+__device__ __forceinline__ void two(int op, T (&r)[1 << R], T (&i)[1 << R], const T *m) {
+    if (op == OP_DENSE2) ap_dense2<T, 1 << R, A, B>(r, i, m);
+    else if (op == OP_DIAG2) ap_diag2<T, 1 << R, A, B>(r, i, m);
+    else ap_perm2<T, 1 << R, A, B>(r, i, m);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void apply_gate(int op, int code, const T *m, T (&r)[1 << R], T (&i)[1 << R]) {
     if (op == OP_DENSE1 || op == OP_DIAG1) {
-        switch (code) { SV_1Q(0) SV_1Q(1) SV_1Q(2) SV_1Q(3) default: break; }
+        switch (code) {
+            case 0: one<T, R, 0>(op, r, i, m); break;
+            case 1: one<T, R, 1>(op, r, i, m); break;
+            case 2: one<T, R, 2>(op, r, i, m); break;
+            case 3: one<T, R, 3>(op, r, i, m); break;
+            case 4: if constexpr (R > 4) one<T, R, 4>(op, r, i, m); break;
+            default: break;
+        }
     } else {
-        switch (code) { SV_2Q(0, 1) SV_2Q(0, 2) SV_2Q(0, 3) SV_2Q(1, 2) SV_2Q(1, 3) SV_2Q(2, 3) default: break; }
+        switch (code) {
+            case 0 * 8 + 1: two<T, R, 0, 1>(op, r, i, m); break;
+            case 0 * 8 + 2: two<T, R, 0, 2>(op, r, i, m); break;
+            case 0 * 8 + 3: two<T, R, 0, 3>(op, r, i, m); break;
+            case 1 * 8 + 2: two<T, R, 1, 2>(op, r, i, m); break;
+            case 1 * 8 + 3: two<T, R, 1, 3>(op, r, i, m); break;
+            case 2 * 8 + 3: two<T, R, 2, 3>(op, r, i, m); break;
+            case 0 * 8 + 4: if constexpr (R > 4) two<T, R, 0, 4>(op, r, i, m); break;
+            case 1 * 8 + 4: if constexpr (R > 4) two<T, R, 1, 4>(op, r, i, m); break;
+            case 2 * 8 + 4: if constexpr (R > 4) two<T, R, 2, 4>(op, r, i, m); break;
+            case 3 * 8 + 4: if constexpr (R > 4) two<T, R, 3, 4>(op, r, i, m); break;
+            default: break;
+        }
     }
-#undef SV_1Q
-#undef SV_2Q
 }
 
 // One register group over the chunk in shared memory.
-template <typename T, int NC, int KU>
-__device__ __forceinline__ void run_segment(typename V2<T>::type *buf, int c, const DevSeg &sg,
-                                            const DevGate<T> *__restrict__ gates, int ctid) {
+template <typename T, int R, int NC>
+__device__ __forceinline__ void run_segment(typename V2<T>::type *buf, const DevSeg &sg,
+                                            const DevGate<T> *__restrict__ gates, int ctid, const int *swz,
+                                            int c) {
     using T2 = typename V2<T>::type;
-    const int p0 = sg.pos[0], p1 = sg.pos[1], p2 = sg.pos[2], p3 = sg.pos[3];
-    int off[NA];
+    constexpr int NA = 1 << R;
+    const int lane = ctid & 31, warp = ctid >> 5;
+    // addresses of the group's amplitudes relative to the group base, natural and swizzled
+    int off[NA], soff[NA];
+    {
+        int po[R], pf[R];
 #pragma unroll
-    for (int b = 0; b < NA; ++b)
-        off[b] = ((b & 1) << p0) | (((b >> 1) & 1) << p1) | (((b >> 2) & 1) << p2) | (((b >> 3) & 1) << p3);
+        for (int j = 0; j < R; ++j) {
+            po[j] = 1 << sg.pos[j];
+            pf[j] = po[j] ^ swz[sg.pos[j]];
+        }
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            int o = 0, f = 0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
+            off[b] = o;
+            soff[b] = f;
+        }
+    }
     const int G = 1 << (c - R);
-    for (int g0 = ctid; g0 < G; g0 += NC * KU) {
-        T re[KU][NA], im[KU][NA];
-        int base[KU];
+    const int nrest = sg.nrest;
+    for (int g = ctid; g < G; g += NC) {
+        // group base: lane bits, then warp/iteration bits
+        int base = 0, fb = 0;
 #pragma unroll
-        for (int u = 0; u < KU; ++u) {
-            const int g = g0 + u * NC;
-            base[u] = insert0(insert0(insert0(insert0(g, p0), p1), p2), p3);
-            if (g < G) {
+        for (int j = 0; j < 5; ++j)
+            if ((lane >> j) & 1) { base |= 1 << sg.lane[j]; fb ^= swz[sg.lane[j]]; }
+        const int hi = (g >> 5);
+        for (int j = 0; j < nrest; ++j)
+            if ((hi >> j) & 1) { base |= 1 << sg.rest[j]; fb ^= swz[sg.rest[j]]; }
+        (void)warp;
+        const int sbase = base ^ fb;
+        T re[NA], im[NA];
+        if (sg.flags & 1) {
 #pragma unroll
-                for (int b = 0; b < NA; ++b) {
-                    const T2 v = buf[base[u] + off[b]];
-                    re[u][b] = v.x;
-                    im[u][b] = v.y;
-                }
-            }
+            for (int b = 0; b < NA; ++b) { const T2 v = buf[base | off[b]]; re[b] = v.x; im[b] = v.y; }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NA; ++b) { const T2 v = buf[sbase ^ soff[b]]; re[b] = v.x; im[b] = v.y; }
         }
         for (int gi = sg.g0; gi < sg.g1; ++gi) {
-            const DevGate<T> *g = gates + gi;
-            const int op = g->op, code = g->code;
-#pragma unroll
-            for (int u = 0; u < KU; ++u) apply_gate<T>(g, op, code, re[u], im[u]);
+            const DevGate<T> *gp = gates + gi;
+            apply_gate<T, R>(gp->op, gp->code, gp->m, re, im);
         }
+        if (sg.flags & 2) {
 #pragma unroll
-        for (int u = 0; u < KU; ++u) {
-            if (g0 + u * NC < G) {
+            for (int b = 0; b < NA; ++b) { T2 v; v.x = re[b]; v.y = im[b]; buf[base | off[b]] = v; }
+        } else {
 #pragma unroll
-                for (int b = 0; b < NA; ++b) {
-                    T2 v;
-                    v.x = re[u][b];
-                    v.y = im[u][b];
-                    buf[base[u] + off[b]] = v;
-                }
-            }
+            for (int b = 0; b < NA; ++b) { T2 v; v.x = re[b]; v.y = im[b]; buf[sbase ^ soff[b]] = v; }
         }
     }
 }
 
-template <typename T, int NC, int KU>
+// Tensor coordinates of the box that holds amplitude index x (box bits of x are zero).
+template <typename T2>
+__device__ __forceinline__ void gather_coords(const GatherArgs &ga, int64_t x, int *coord) {
+    for (int d = 0; d < ga.rank; ++d) {
+        const int w = ga.s[d + 1] - ga.s[d];
+        int64_t v = (x >> ga.s[d]) & ((int64_t(1) << w) - 1);
+        if (d == 0 && sizeof(T2) == 16) v *= 2;  // complex128: two doubles per amplitude
+        coord[d] = (int)v;
+    }
+    for (int d = ga.rank; d < 5; ++d) coord[d] = 0;
+}
+
+// Amplitude index of the first element of copy t of gathered chunk j.
+__device__ __forceinline__ int64_t gather_origin(const GatherArgs &ga, int64_t j, int t) {
+    int64_t x = 0;
+    for (int k = 0; k < ga.nouter; ++k)
+        if ((j >> k) & 1) x |= int64_t(1) << ga.outer[k];
+    for (int k = 0; k < ga.nloop; ++k)
+        if ((t >> k) & 1) x |= int64_t(1) << ga.loop[k];
+    return x;
+}
+
+template <typename T, int R, int NC>
 __global__ void __launch_bounds__(NC + 32, 1)
     k_block(typename V2<T>::type *__restrict__ state, int c, int64_t nchunks, int nbuf,
-            const DevSeg *__restrict__ segs, int nseg, const DevGate<T> *__restrict__ gates, int *err) {
+            const unsigned char *__restrict__ prog, int nseg, int ngate, int *err,
+            const __grid_constant__ CUtensorMap tmap, const GatherArgs ga_in) {
     using T2 = typename V2<T>::type;
+    __shared__ GatherArgs ga;  // gathered chunks (rank > 0); rank 0 = contiguous chunk j
+    if (threadIdx.x == 0) ga = ga_in;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int chunk_amps = 1 << c;
     const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
     T2 *bufs = reinterpret_cast<T2 *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)nbuf * chunk_bytes);
+    // block program copied into shared memory: segments then gates (16-byte aligned)
+    const int seg_bytes = (int)((nseg * sizeof(DevSeg) + 15) & ~size_t(15));
+    const int prog_bytes = seg_bytes + ngate * (int)sizeof(DevGate<T>);
+    unsigned char *sprog = smem + (size_t)nbuf * chunk_bytes;
+    const DevSeg *segs = reinterpret_cast<const DevSeg *>(sprog);
+    const DevGate<T> *gates = reinterpret_cast<const DevGate<T> *>(sprog + seg_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sprog + ((prog_bytes + 15) & ~15));
     uint64_t *empty = full + nbuf;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + nbuf);
+    __shared__ int swz[24];
 
+    for (int k = threadIdx.x * 16; k < prog_bytes; k += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(sprog + k) = *reinterpret_cast<const uint4 *>(prog + k);
+    if (threadIdx.x < 24) swz[threadIdx.x] = sizeof(T2) == 8 ? c_swz64[threadIdx.x] : c_swz128[threadIdx.x];
     if (threadIdx.x == 0) {
         for (int s = 0; s < nbuf; ++s) {
             ptx::mbar_init(&full[s], 1);
@@ -240,12 +320,20 @@ __global__ void __launch_bounds__(NC + 32, 1)
                 }
             }
             const int64_t j = blockIdx.x + it * gridDim.x;
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(state + j * chunk_amps);
             unsigned char *dst = reinterpret_cast<unsigned char *>(bufs + (size_t)s * chunk_amps);
             ptx::mbar_arrive_expect_tx(&full[s], chunk_bytes);
-            for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
-                const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
-                ptx::bulk_g2s(dst + o, src + o, b, &full[s]);
+            if (ga.rank > 0) {
+                for (int t = 0; t < (1 << ga.nloop); ++t) {
+                    int coord[5];
+                    gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
+                    ptx::tensor_g2s(dst + (size_t)t * ga.box_amps * sizeof(T2), &tmap, coord, ga.rank, &full[s]);
+                }
+            } else {
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(state + j * chunk_amps);
+                for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+                    const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
+                    ptx::bulk_g2s(dst + o, src + o, b, &full[s]);
+                }
             }
             ++issued;
         }
@@ -268,18 +356,25 @@ __global__ void __launch_bounds__(NC + 32, 1)
         if (*abort_flag) break;
         T2 *buf = bufs + (size_t)s * chunk_amps;
         for (int si = 0; si < nseg; ++si) {
-            const DevSeg sg = segs[si];
-            run_segment<T, NC, KU>(buf, c, sg, gates, ctid);
+            run_segment<T, R, NC>(buf, segs[si], gates, ctid, swz, c);
             if (si == nseg - 1) ptx::fence_proxy_async_smem();
             ptx::named_bar_sync(1, NC);
         }
         if (nseg == 0) ptx::fence_proxy_async_smem();
         if (ctid == 0) {
-            unsigned char *dstg = reinterpret_cast<unsigned char *>(state + j * chunk_amps);
             const unsigned char *srcs = reinterpret_cast<const unsigned char *>(buf);
-            for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
-                const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
-                ptx::bulk_s2g(dstg + o, srcs + o, b);
+            if (ga.rank > 0) {
+                for (int t = 0; t < (1 << ga.nloop); ++t) {
+                    int coord[5];
+                    gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
+                    ptx::tensor_s2g(&tmap, coord, ga.rank, srcs + (size_t)t * ga.box_amps * sizeof(T2));
+                }
+            } else {
+                unsigned char *dstg = reinterpret_cast<unsigned char *>(state + j * chunk_amps);
+                for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+                    const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
+                    ptx::bulk_s2g(dstg + o, srcs + o, b);
+                }
             }
             ptx::bulk_commit();
             if (nbuf >= 3) {
@@ -296,45 +391,140 @@ __global__ void __launch_bounds__(NC + 32, 1)
     if (ctid == 0) ptx::bulk_wait<0>();
 }
 
-template <typename T, int NC, int KU>
-void launch_typed(void *state, int n, int c, const void *segs, int nseg, const void *gates, int *err,
-                  cudaStream_t st) {
+template <typename T, int R, int NC>
+void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st,
+                  const CUtensorMap &tmap, const GatherArgs &ga) {
     using T2 = typename V2<T>::type;
-    const int ce = c < n ? c : n;
     const size_t chunk_bytes = (size_t(1) << ce) * sizeof(T2);
     const int64_t nchunks = int64_t(1) << (n - ce);
-    const size_t extra = 2 * 8 * 4 + 16;  // barriers + abort flag (up to 4 buffers)
+    const size_t seg_bytes = (nseg * sizeof(DevSeg) + 15) & ~size_t(15);
+    const size_t prog_bytes = (seg_bytes + ngate * sizeof(DevGate<T>) + 15) & ~size_t(15);
+    const size_t extra = prog_bytes + 2 * 8 * 4 + 16;  // program + barriers + abort flag
     int nbuf = 3;
-    const size_t max_smem = 227 * 1024;
+    const size_t max_smem = 227 * 1024 - 1024;  // minus the static swizzle table (1 KiB aligned)
     while (nbuf > 1 && nbuf * chunk_bytes + extra > max_smem) --nbuf;
     const size_t smem = nbuf * chunk_bytes + extra;
-    if (smem > max_smem) fail(SV_ERR_UNSUPPORTED, "chunk does not fit in shared memory");
-    auto kern = k_block<T, NC, KU>;
+    if (smem > max_smem) fail(SV_ERR_UNSUPPORTED, "chunk and section program do not fit in shared memory");
+    auto kern = k_block<T, R, NC>;
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(block)");
     int per_sm = 0;
     check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, smem), "occupancy(block)");
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm);
-    kern<<<(unsigned)grid, NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const DevSeg *)segs, nseg,
-                                                (const DevGate<T> *)gates, err);
+    kern<<<(unsigned)grid, NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
+                                                ngate, err, tmap, ga);
     check_cuda(cudaGetLastError(), "block kernel launch");
+}
+
+template <typename T, int R, int NC>
+void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st) {
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    GatherArgs ga{};
+    launch_typed<T, R, NC>(state, n, ce, prog, nseg, ngate, err, st, none, ga);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        check_cuda(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q),
+                   "cudaGetDriverEntryPointByVersion(cuTensorMapEncodeTiled)");
+        if (q != cudaDriverEntryPointSuccess || !p) fail(SV_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of the whole state viewed with the gathered layout's dimensions: dimension d
+// covers index bits [s[d], s[d+1]), its box the chunk run at its bottom.
+CUtensorMap make_gather_map(void *state, int n, const GatherLayout &lay, int elem_bytes) {
+    const GatherArgs &ga = lay.args;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5];
+    const int dup = elem_bytes == 16 ? 2 : 1;  // complex128 as two doubles
+    for (int d = 0; d < ga.rank; ++d) {
+        dims[d] = (cuuint64_t(1) << (ga.s[d + 1] - ga.s[d])) * (d == 0 ? dup : 1);
+        box[d] = (cuuint32_t(1) << lay.box_len[d]) * (d == 0 ? dup : 1);
+        estr[d] = 1;
+        if (d > 0) strides[d - 1] = (cuuint64_t(1) << ga.s[d]) * (cuuint64_t)elem_bytes;
+    }
+    (void)n;
+    CUtensorMap m;
+    const CUresult r = encode_tiled()(&m, elem_bytes == 16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_INT64,
+                                      (cuuint32_t)ga.rank, state, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SV_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return m;
 }
 
 }  // namespace
 
 size_t devgate_bytes(int dtype) { return dtype == SV_C64 ? sizeof(DevGate<float>) : sizeof(DevGate<double>); }
 
-void launch_block(int dtype, void *state, int n, int c, const void *dev_segs, int nseg, const void *dev_gates,
-                  int ngates, int *dev_err, int threads, cudaStream_t st) {
-    (void)ngates;
-    (void)threads;
+int block_threads(int ce, int seg_bits) {
+    const int groups = 1 << (ce - seg_bits);
+    const int cap = seg_bits >= 5 ? 256 : 512;  // 2^5 amplitudes per thread: 256 threads fit the registers
+    const int nc = groups >= 512 ? 512 : (groups >= 256 ? 256 : 128);
+    return nc < cap ? nc : cap;
+}
+
+void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, int nseg, int ngates, int *dev_err,
+                  int seg_bits, cudaStream_t st) {
     const int ce = c < n ? c : n;
-    if (ce < SEG_BITS) fail(SV_ERR_UNSUPPORTED, "blocked path needs a chunk of at least 4 bits");
-    if (dtype == SV_C64)
-        launch_typed<float, 256, 2>(state, n, c, dev_segs, nseg, dev_gates, dev_err, st);
-    else
-        launch_typed<double, 256, 1>(state, n, c, dev_segs, nseg, dev_gates, dev_err, st);
+    if (ce < 4) fail(SV_ERR_UNSUPPORTED, "blocked path needs a chunk of at least 4 bits");
+    const int r = seg_bits < ce ? seg_bits : ce;  // the register groups were built with this width
+    const int nc = block_threads(ce, r);
+    if (dtype == SV_C64) {
+        if (r == 4) {
+            if (nc == 512) launch_typed<float, 4, 512>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+            else if (nc == 256) launch_typed<float, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+            else launch_typed<float, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+        } else {
+            if (nc == 256) launch_typed<float, 5, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+            else launch_typed<float, 5, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+        }
+    } else {
+        if (nc >= 256) launch_typed<double, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+        else launch_typed<double, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
+    }
+}
+
+void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay, const void *dev_prog, int nseg,
+                         int ngates, int *dev_err, int seg_bits, cudaStream_t st) {
+    const int ce = lay.ce;
+    if (ce < 4) fail(SV_ERR_UNSUPPORTED, "blocked path needs a chunk of at least 4 bits");
+    if (reinterpret_cast<uintptr_t>(state) % 16) fail(SV_ERR_ARG, "state buffer not 16-byte aligned");
+    const int elem = dtype == SV_C64 ? 8 : 16;
+    // every tensor copy lands on a 128-byte boundary of the chunk buffer
+    if ((size_t)lay.args.box_amps * elem < 128)
+        fail(SV_ERR_UNSUPPORTED, "gathered chunk boxes smaller than 128 bytes (pin more low bits)");
+    const CUtensorMap m = make_gather_map(state, n, lay, elem);
+    const int r = seg_bits < ce ? seg_bits : ce;
+    const int nc = block_threads(ce, r);
+    const GatherArgs &ga = lay.args;
+    if (dtype == SV_C64) {
+        if (r == 4) {
+            if (nc == 512) launch_typed<float, 4, 512>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+            else if (nc == 256) launch_typed<float, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+            else launch_typed<float, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+        } else {
+            if (nc == 256) launch_typed<float, 5, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+            else launch_typed<float, 5, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+        }
+    } else {
+        if (nc >= 256) launch_typed<double, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+        else launch_typed<double, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
+    }
 }
 
 }  // namespace sv

@@ -32,6 +32,9 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     const int width = std::min(c, n);
     const int target = std::min(c - o.reserve, n);
     if (target < 1) fail(SV_ERR_ARG, "chunk too small");
+    const int pinned = o.gather_pinned;
+    if (pinned < 0 || pinned > n || (pinned && target - pinned < 2))
+        fail(SV_ERR_ARG, "gather_pinned leaves no room for a 2-qubit gate");
 
     struct PG {
         int64_t gi;
@@ -46,8 +49,9 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     plan->c = c;
     plan->reserve = o.reserve;
     plan->restore = o.restore_layout ? 1 : 0;
-    plan->seg_bits = SEG_BITS;
+    plan->seg_bits = (o.seg_bits == 4 || o.seg_bits == 5) ? o.seg_bits : 5;
     plan->use_tc = o.use_tc;
+    plan->pinned = pinned;
     plan->keys.reserve((size_t)n_gates);
 
     std::vector<int32_t> lab(n);
@@ -95,6 +99,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
                 cnt += popc(fresh);
             }
         };
+        for (int p = 0; p < pinned; ++p) try_add(1ull << pinv[p]);  // gathered chunks keep the low bits
         try_add(remaining.front().vmask);
         for (const PG &g : remaining) {
             if (cnt >= target) break;
@@ -104,13 +109,13 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             if (cnt >= target) break;
             if (g.nq == 1) try_add(g.vmask);
         }
-        for (int p = 0; p < width && cnt < target; ++p) try_add(1ull << pinv[p]);
+        for (int p = 0; p < (pinned ? n : width) && cnt < target; ++p) try_add(1ull << pinv[p]);
 
-        // chunk_swap round
+        // chunk_swap round (none for gathered chunks: the section fetches its bits in place)
         PlanOp round;
         round.kind = 1;
         std::vector<int32_t> incoming, vacated;
-        for (int v = 0; v < n; ++v)
+        for (int v = 0; v < n && !pinned; ++v)
             if (((chosen >> v) & 1) && m[v] >= width) incoming.push_back(v);
         for (int p = 0; p < width; ++p)
             if (!((chosen >> pinv[p]) & 1)) vacated.push_back(p);
@@ -127,7 +132,10 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
 
         // scan REMAINING with QB_BLOCKED
         PlanOp block;
-        block.kind = 2;
+        block.kind = pinned ? 4 : 2;
+        if (pinned)
+            for (int v = 0; v < n; ++v)
+                if ((chosen >> v) & 1) block.mask |= 1ull << m[v];
         uint64_t blocked = 0;
         next.clear();
         for (const PG &g : remaining) {
@@ -191,19 +199,33 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
 
     // register groups per block (for statistics and execution)
     int nseg = 0;
-    for (const PlanOp &op : plan->ops)
-        if (op.kind == 2) nseg += (int)segment_block(op.gates, std::min(c, n)).size();
+    for (const PlanOp &op : plan->ops) {
+        if (op.kind == 2) nseg += (int)segment_block(op.gates, std::min(c, n), plan->seg_bits, 8).size();
+        if (op.kind == 4) {
+            const GatherLayout L = gather_layout(op.mask, n, 8);
+            std::vector<BlockGate> loc = op.gates;
+            for (BlockGate &g : loc)
+                for (int j = 0; j < g.nq; ++j) g.phys[j] = L.local_of[g.phys[j]];
+            nseg += (int)segment_block(loc, L.ce, plan->seg_bits, 8).size();
+        }
+    }
     plan->n_segments = nseg;
     return plan;
 }
 
 // ---------------------------------------------------------------------------------------
 // Register groups.  Inside a blocking section each chunk lives in shared memory; a group is
-// a set of SEG_BITS chunk bits whose 2^SEG_BITS amplitudes one thread holds in registers
-// while it applies every gate of the group.  Gates are taken greedily in block order; a gate
-// that does not fit is deferred and blocks its bits for the rest of the group (so per-qubit
-// gate order is kept), the same rule the transpiler uses one level up.
-std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width) {
+// a set of r chunk bits whose 2^r amplitudes one thread holds in registers while it applies
+// every gate of the group.  Gates are taken greedily in section order; a gate that does not
+// fit is deferred and blocks its bits for the rest of the group (so per-qubit gate order is
+// kept), the same rule the transpiler uses one level up.
+//
+// Lane layout: the lanes that share a shared-memory wavefront (16 for 8-byte amplitudes, 8 for
+// 16-byte ones) must enumerate distinct bank slots.  A chunk bit k contributes the slot vector
+// w(k) = 2^k for k < SB and the swizzle pattern V[k] above; the first lane bits are chosen
+// greedily (ascending bit order) among the bits outside the group so that their w(k) are
+// linearly independent over GF(2).
+std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes) {
     std::vector<HostSeg> segs;
     std::vector<int32_t> pending(gates.size());
     std::iota(pending.begin(), pending.end(), 0);
@@ -212,14 +234,16 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
         if (g.nq == 2) mk |= 1ull << g.phys[1];
         return mk;
     };
+    const int rr = std::min(r, width);
     std::vector<int32_t> rest;
     while (!pending.empty()) {
         uint64_t set = 0, blocked = 0;
-        HostSeg s{};
+        HostSeg s;
+        s.r = rr;
         rest.clear();
         for (int32_t idx : pending) {
             const uint64_t mk = mask_of(gates[idx]);
-            if ((mk & blocked) == 0 && popc(set | mk) <= SEG_BITS) {
+            if ((mk & blocked) == 0 && popc(set | mk) <= rr) {
                 set |= mk;
                 s.gates.push_back(idx);
             } else {
@@ -227,22 +251,112 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
                 rest.push_back(idx);
             }
         }
-        // pad with the highest unused chunk bits (keeps the low bits spread across lanes)
-        for (int p = width - 1; p >= 0 && popc(set) < SEG_BITS; --p)
+        // pad with the highest unused chunk bits (keeps the low bits free for the lanes)
+        for (int p = width - 1; p >= 0 && popc(set) < rr; --p)
             if (!((set >> p) & 1)) set |= 1ull << p;
         int k = 0;
-        for (int p = 0; p < 64 && k < SEG_BITS; ++p)
+        for (int p = 0; p < width && k < rr; ++p)
             if ((set >> p) & 1) s.pos[k++] = p;
         segs.push_back(std::move(s));
         pending.swap(rest);
     }
+    // lane layouts
+    const int sb = elem_bytes == 8 ? 4 : 3;
+    const int *swz = elem_bytes == 8 ? kSwz64 : kSwz128;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        HostSeg &s = segs[i];
+        uint64_t in = 0;
+        for (int k = 0; k < s.r; ++k) in |= 1ull << s.pos[k];
+        std::vector<int> outside;
+        for (int p = 0; p < width; ++p)
+            if (!((in >> p) & 1)) outside.push_back(p);
+        std::vector<int> lanes, others;
+        int basis[8] = {0};  // GF(2) echelon basis by leading bit
+        for (int p : outside) {
+            if ((int)lanes.size() < sb) {
+                int v = p < sb ? (1 << p) : swz[p];
+                for (int b = sb - 1; b >= 0 && v; --b)
+                    if ((v >> b) & 1) {
+                        if (basis[b]) v ^= basis[b];
+                        else { basis[b] = v; v = -1; break; }
+                    }
+                if (v == -1) { lanes.push_back(p); continue; }
+            }
+            others.push_back(p);
+        }
+        // complete the lane bits (5 in all) from the remaining bits, lowest first
+        std::vector<int> order = lanes;
+        std::vector<int> rem;
+        for (int p : others) {
+            if ((int)order.size() < 5) order.push_back(p);
+            else rem.push_back(p);
+        }
+        // if fewer than sb independent bits existed, the first lanes are whatever is available
+        for (int j = 0; j < 5; ++j) s.lane[j] = j < (int)order.size() ? order[j] : 0;
+        s.nrest = (int)rem.size();
+        for (int j = 0; j < s.nrest; ++j) s.rest[j] = rem[j];
+        s.flags = (i == 0 ? 1 : 0) | (i + 1 == segs.size() ? 2 : 0);
+    }
     return segs;
+}
+
+// Gathered chunk layout: runs of consecutive chunk bits; the run at bit 0 and the (up to) four
+// longest other runs start tensor dimensions (boxes of at most 8 bits, 7 for the doubled
+// complex128 innermost dimension), everything else in the chunk is a loop bit.
+GatherLayout gather_layout(uint64_t mask, int n, int elem_bytes) {
+    GatherLayout L;
+    for (int b = 0; b < 64; ++b) L.local_of[b] = -1;
+    std::vector<std::pair<int, int>> runs;  // (start, length)
+    for (int b = 0; b < n;) {
+        if ((mask >> b) & 1) {
+            const int s = b;
+            while (b < n && ((mask >> b) & 1)) ++b;
+            runs.emplace_back(s, b - s);
+        } else {
+            ++b;
+        }
+    }
+    if (runs.empty() || runs[0].first != 0) fail(SV_ERR_PLAN, "a gathered chunk must contain bit 0");
+    std::vector<int> idx;
+    for (int i = 1; i < (int)runs.size(); ++i) idx.push_back(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return runs[a].second > runs[b].second; });
+    if (idx.size() > 4) idx.resize(4);
+    std::sort(idx.begin(), idx.end());
+    std::vector<int> dims{0};
+    dims.insert(dims.end(), idx.begin(), idx.end());
+    GatherArgs &A = L.args;
+    A.rank = (int)dims.size();
+    int k = 0, box_bits = 0;
+    for (int d = 0; d < A.rank; ++d) {
+        A.s[d] = runs[dims[d]].first;
+        const int cap = d == 0 ? (elem_bytes == 8 ? 8 : 7) : 8;
+        L.box_len[d] = std::min(runs[dims[d]].second, cap);
+        for (int b = A.s[d]; b < A.s[d] + L.box_len[d]; ++b) L.local_of[b] = k++;
+        box_bits += L.box_len[d];
+    }
+    A.s[A.rank] = n;
+    A.nloop = 0;
+    A.nouter = 0;
+    for (int b = 0; b < n; ++b) {
+        if ((mask >> b) & 1) {
+            if (L.local_of[b] < 0) {
+                if (A.nloop >= 16) fail(SV_ERR_UNSUPPORTED, "gathered chunk has too many scattered bits");
+                A.loop[A.nloop++] = (int8_t)b;
+                L.local_of[b] = k++;
+            }
+        } else {
+            A.outer[A.nouter++] = (int8_t)b;
+        }
+    }
+    A.box_amps = 1 << box_bits;
+    L.ce = k;
+    return L;
 }
 
 template <typename T>
 void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevGate<T> &out) {
     auto local = [&](int phys) {
-        for (int k = 0; k < SEG_BITS; ++k)
+        for (int k = 0; k < seg.r; ++k)
             if (seg.pos[k] == phys) return k;
         fail(SV_ERR_PLAN, "gate bit outside its register group");
     };
@@ -279,7 +393,7 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
     }
     out.a = la;
     out.b = lb;
-    out.code = la * SEG_BITS + lb;
+    out.code = la * 8 + lb;
     bool diag = true, perm = true;
     for (int r = 0; r < 4; ++r) {
         int ones = 0;

@@ -71,6 +71,63 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+// Tensor (tiled) copy global -> shared of one box at integer coordinates c[0..rank), completing
+// on an mbarrier.  `tmap` is the generic address of a CUtensorMap kernel parameter.
+__device__ __forceinline__ void tensor_g2s(void *dst, const void *tmap, const int *c, int rank, uint64_t *bar) {
+    const uint32_t d = smem_addr(dst), b = smem_addr(bar);
+    const uint64_t m = reinterpret_cast<uint64_t>(tmap);
+    switch (rank) {
+        case 1:
+            asm volatile("cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];"
+                         ::"r"(d), "l"(m), "r"(c[0]), "r"(b) : "memory");
+            break;
+        case 2:
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                         ::"r"(d), "l"(m), "r"(c[0]), "r"(c[1]), "r"(b) : "memory");
+            break;
+        case 3:
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(d), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(b) : "memory");
+            break;
+        case 4:
+            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                         ::"r"(d), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(b) : "memory");
+            break;
+        default:
+            asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                         ::"r"(d), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(b) : "memory");
+            break;
+    }
+}
+
+// Tensor (tiled) copy shared -> global of one box, tracked by bulk groups.
+__device__ __forceinline__ void tensor_s2g(const void *tmap, const int *c, int rank, const void *src) {
+    const uint32_t s = smem_addr(src);
+    const uint64_t m = reinterpret_cast<uint64_t>(tmap);
+    switch (rank) {
+        case 1:
+            asm volatile("cp.async.bulk.tensor.1d.global.shared::cta.tile.bulk_group [%0, {%1}], [%2];"
+                         ::"l"(m), "r"(c[0]), "r"(s) : "memory");
+            break;
+        case 2:
+            asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+                         ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(s) : "memory");
+            break;
+        case 3:
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];"
+                         ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(s) : "memory");
+            break;
+        case 4:
+            asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+                         ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(s) : "memory");
+            break;
+        default:
+            asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];"
+                         ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(s) : "memory");
+            break;
+    }
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 template <int N>

@@ -34,9 +34,10 @@ struct BlockGate {
 };
 
 struct PlanOp {
-    int32_t kind;  // 1 = chunk_swap round, 2 = block, 3 = output-reordering round
+    int32_t kind;  // 1 = chunk_swap round, 2 = block, 3 = output-reordering round, 4 = gathered block
     std::vector<std::pair<int32_t, int32_t>> pairs;
     std::vector<BlockGate> gates;
+    uint64_t mask = 0;  // chunk bits of a gathered block
 };
 
 struct GateKey {
@@ -49,7 +50,7 @@ struct GateKey {
 }  // namespace sv
 
 struct sv_plan {
-    int32_t n = 0, c = 0, reserve = 0, restore = 1, seg_bits = 4, use_tc = 0;
+    int32_t n = 0, c = 0, reserve = 0, restore = 1, seg_bits = 5, use_tc = 0, pinned = 0;
     std::vector<sv::PlanOp> ops;
     std::vector<int32_t> final_map;
     std::vector<sv::GateKey> keys;  // structure of the gate list it was made from
@@ -61,36 +62,81 @@ namespace sv {
 sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o);
 
 // ------------------------------------------------------------------ block programs
-constexpr int SEG_BITS = 4;            // amplitudes per register group = 2^SEG_BITS
-constexpr int MAX_SEGS_PER_BLOCK = 512;
-constexpr int MAX_GATES_PER_BLOCK = 1024;
+constexpr int SEG_BITS = 4;      // default register-group width (amplitudes per group = 2^SEG_BITS)
+constexpr int MAX_SEG_BITS = 5;
+
+// Shared-memory swizzle of a chunk: amplitude i lives in slot i ^ F(i), F(i) = XOR of V[k] over
+// the set bits k >= SB of i (SB = 4 for complex64, 3 for complex128).  The V are distinct
+// non-powers-of-two below 2^SB where possible, so that any SB of the chunk bits outside a
+// register group, plus the low bits, enumerate distinct banks.
+#define SV_SWZ64_LIST 0, 0, 0, 0, 3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 3, 5, 6, 7, 9, 10, 11, 12, 13
+#define SV_SWZ128_LIST 0, 0, 0, 3, 5, 6, 7, 3, 5, 6, 7, 3, 5, 6, 7, 3, 5, 6, 7, 3, 5, 6, 7, 3
+constexpr int kSwz64[24] = {SV_SWZ64_LIST};
+constexpr int kSwz128[24] = {SV_SWZ128_LIST};
 
 // Gate op-codes inside a segment.
 enum : int32_t { OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG1 = 2, OP_DIAG2 = 3, OP_PERM2 = 4 };
 
+// Register group as the kernel reads it.  A thread's group index g enumerates the chunk bits
+// outside the group: g bits 0..4 land on lane[0..4], the higher bits on rest[0..nrest).
 struct DevSeg {
-    int32_t pos[SEG_BITS];  // physical bits (ascending) held in registers
-    int32_t g0, g1;         // gate range [g0, g1) in the block's gate array
+    int8_t pos[8];    // group bits (ascending); r of them used
+    int8_t lane[5];
+    int8_t nrest;
+    int8_t flags;     // 1: read the natural (unswizzled) layout, 2: write the natural layout
+    int8_t r;
+    int8_t rest[16];
+    int16_t g0, g1;   // gate range [g0, g1) in the section's gate array
 };
+static_assert(sizeof(DevSeg) == 36, "DevSeg layout");
 
 template <typename T>
 struct DevGate {
     int32_t op;     // OP_*
     int32_t a, b;   // local register bits (a < b for 2-qubit ops)
-    int32_t code;   // pair index of (a, b) / bit index a, for kernel dispatch
-    T m[32];        // row-major complex matrix in local basis bit a + 2*bit b (diag: 4 entries)
+    int32_t code;   // a for 1-qubit ops, a * 8 + b for 2-qubit ops
+    T m[32];        // row-major complex matrix in local basis bit a + 2*bit b (diag: the diagonal)
 };
 
 struct HostSeg {
-    int32_t pos[SEG_BITS];
-    std::vector<int32_t> gates;  // indices into block gate list
+    int r = SEG_BITS;
+    int32_t pos[8] = {0};
+    int32_t lane[5] = {0};
+    int32_t rest[16] = {0};
+    int nrest = 0;
+    int flags = 0;
+    std::vector<int32_t> gates;  // indices into the section's gate list
 };
 
-// Split a block's gates (physical bits < c) into register groups of at most SEG_BITS bits.
-std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int c);
+// Split a section's gates (physical bits < width) into register groups of at most r bits,
+// and choose each group's lane layout for elements of elem_bytes bytes.
+std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes);
 
 template <typename T>
 void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevGate<T> &out);
+
+// Gathered chunk: the state is viewed as a tensor of rank <= 5 whose dimension d covers the
+// index bits [s[d], s[d+1]); each dimension starts with a run of chunk bits (its box, at most
+// 8 bits), the bits above it up to the next dimension are addressed by coordinates.  Chunk bits
+// outside the boxes are "loop" bits: one tensor copy per value.  Chunk-local bit order: the
+// box bits of dimension 0, 1, ..., then the loop bits.
+struct GatherArgs {
+    int32_t rank;
+    int32_t s[6];          // dimension start bits; s[rank] = n
+    int32_t nouter, nloop;
+    int32_t box_amps;      // amplitudes per tensor copy (2^(box bits))
+    int8_t outer[64];      // chunk-index bit -> state bit
+    int8_t loop[16];       // copy-index bit -> state bit
+};
+
+struct GatherLayout {
+    GatherArgs args{};
+    int box_len[5] = {0};
+    int local_of[64];      // state bit -> chunk-local bit (-1 outside the chunk)
+    int ce = 0;            // chunk bits
+};
+
+GatherLayout gather_layout(uint64_t mask, int n, int elem_bytes);
 
 // ------------------------------------------------------------------ kernels (launchers)
 struct Mat1 { float m[8]; };
@@ -105,8 +151,12 @@ struct PermPlan;  // defined in k_permute.cu
 void launch_permute(int dtype, void *state, int n, const std::vector<std::pair<int32_t, int32_t>> &pairs,
                     cudaStream_t st);
 
-void launch_block(int dtype, void *state, int n, int c, const void *dev_segs, int nseg,
-                  const void *dev_gates, int ngates, int *dev_err, int threads, cudaStream_t st);
+void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, int nseg, int ngates, int *dev_err,
+                  int seg_bits, cudaStream_t st);
+// Blocking section over a gathered chunk (bits in `mask`), fetched and written back with
+// tensor copies.
+void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay, const void *dev_prog, int nseg,
+                         int ngates, int *dev_err, int seg_bits, cudaStream_t st);
 size_t devgate_bytes(int dtype);
 
 // readouts

@@ -233,3 +233,32 @@ def test_torch_buffer_and_stream(sv):
         assert st.device_ptr() == buf.data_ptr()
     got = torch.view_as_complex(buf.view(-1, 2)).cpu().numpy()
     assert_close(got, sim.simulate(n, desc), "c64")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,c,pinned", [(10, 6, 4), (12, 8, 4), (17, 10, 4), (20, 13, 4), (18, 12, 5), (14, 12, 4)])
+def test_gathered_chunks_mixed(sv, dtype, n, c, pinned):
+    desc = _mixed(n, 100, 300 + n + c) + cg.quantum_volume(n, 4, n + 1) + cg.qft(n)
+    ref = sim.simulate(n, desc, 11)
+    got = _run(sv, n, desc, dtype, basis=11, plan_opts=dict(chunk_bits=c, gather_pinned=pinned))
+    assert_close(got, ref, dtype)
+
+
+@pytest.mark.parametrize("seg_bits", [4, 5])
+def test_gathered_quantum_volume_24(sv, seg_bits):
+    n = 24
+    desc = cg.quantum_volume(n, 8, 17)
+    ref = sim.simulate(n, desc)
+    got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=13, gather_pinned=4, seg_bits=seg_bits))
+    assert_close(got, ref, "c64")
+
+
+def test_chunk_larger_than_shared_memory_rejected(sv):
+    n = 16
+    gates = sv.make_gates(cg.quantum_volume(n, 2, 1))
+    for opts in (dict(chunk_bits=16), dict(chunk_bits=16, gather_pinned=4)):
+        with sv.StateVector(n, "c64") as st:
+            st.init_basis(0)
+            with pytest.raises(sv.SVError) as e:
+                st.apply(gates, sv.Plan(n, gates, **opts))
+            assert e.value.status == sv._lib.SV_ERR_UNSUPPORTED

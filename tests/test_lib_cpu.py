@@ -113,3 +113,13 @@ def test_planner_errors(sv):
         sv.Plan(4, bad, chunk_bits=3)
     with pytest.raises(sv.SVError):
         sv.make_gates([("cx", (1, 1), ())])
+
+
+@pytest.mark.parametrize("n,c,pinned", [(6, 4, 1), (12, 8, 3), (16, 10, 4), (30, 13, 4), (30, 13, 3)])
+def test_planner_schedule_parity_gathered(sv, n, c, pinned):
+    for desc in _circuits(n, 7 * n + c):
+        gates = sv.make_gates(desc)
+        p = sv.Plan(n, gates, chunk_bits=c, gather_pinned=pinned)
+        q = planner.plan_blocking(n, desc, c, pinned=pinned)
+        assert p.serialize() == q.serialize()
+        assert p.info().n_swap_rounds == 0

@@ -132,3 +132,20 @@ def test_swap_counts_shrink_with_bigger_chunks():
     gates = cg.quantum_volume(16, 10, 2)
     counts = [planner.plan_blocking(16, gates, c).n_swap_rounds for c in (4, 8, 12, 16)]
     assert counts == sorted(counts, reverse=True) and counts[-1] == 0
+
+
+@pytest.mark.parametrize("n,c,pinned", [(6, 4, 1), (9, 5, 2), (10, 6, 4), (12, 8, 3), (12, 12, 4), (7, 9, 2)])
+def test_gathered_chunks_validity_and_equivalence(n, c, pinned):
+    for gates in _circuits(n, 5 * n + c + pinned):
+        p = planner.plan_blocking(n, gates, c, pinned=pinned)
+        planner.validate(p, gates)
+        assert p.n_swap_rounds == 0
+        for bits, _ in p.blocks():
+            assert set(range(pinned)) <= set(bits) and len(bits) <= min(c, n)
+        ref = sim.simulate(n, gates, 7 % (1 << n))
+        assert np.abs(sim.execute_plan(n, gates, p, 7 % (1 << n)) - ref).max() < 1e-12
+
+
+def test_gathered_chunks_need_room():
+    with pytest.raises(ValueError):
+        planner.plan_blocking(8, [("cx", (0, 5), ())], 4, pinned=3)
