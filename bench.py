@@ -266,6 +266,7 @@ def run_ours(args):
         w["c"] = args.chunk_bits
     n, c, desc = w["n"], w["c"], w["desc"]
     G = len(desc)
+    plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=args.gather_pinned)
     stream = torch.cuda.Stream()
     st = sv.StateVector(n, "c64", stream=stream)
     st.set_profiling(True)
@@ -273,7 +274,7 @@ def run_ours(args):
 
     def step():
         gates = sv.make_gates(desc)
-        plan = sv.Plan(n, gates, chunk_bits=c, seg_bits=args.seg_bits)
+        plan = sv.Plan(n, gates, **plan_opts)
         st.init_basis(0)
         st.apply(gates, plan)
         nrm = st.norm2()
@@ -316,7 +317,7 @@ def run_ours(args):
     blk_ms = ms_block / max(1, n_block)
     perm_ms = ms_perm / max(1, n_perm)
     blk_gbs = sweep_bytes / (blk_ms / 1000.0) / 1e9
-    perm_gbs = sweep_bytes / (perm_ms / 1000.0) / 1e9
+    perm_gbs = sweep_bytes / (perm_ms / 1000.0) / 1e9 if n_perm else None
     dominant = "k_block" if ms_block >= ms_perm else "k_permute"
     dom_src = "paper_2102_02957_gb300/csrc/k_block.cu" if dominant == "k_block" else \
         "paper_2102_02957_gb300/csrc/k_permute.cu"
@@ -345,11 +346,11 @@ def run_ours(args):
         h_in[0] = 1.0
         h_out = torch.empty(2 << n, dtype=torch.float32).pin_memory()
         gates = sv.make_gates(desc)
-        plan = sv.Plan(n, gates, chunk_bits=c)
+        plan = sv.Plan(n, gates, **plan_opts)
 
         def e2e_step():
             g = sv.make_gates(desc)
-            p = sv.Plan(n, g, chunk_bits=c)
+            p = sv.Plan(n, g, **plan_opts)
             st.set_state(h_in.data_ptr())
             st.apply(g, p)
             st.get_state(h_out.data_ptr())
@@ -405,8 +406,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
-    ap.add_argument("--seg-bits", type=int, default=5, help="register-group width inside a chunk (4 or 5)")
+    ap.add_argument("--seg-bits", type=int, default=4, help="register-group width inside a chunk (4 or 5)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the workload's chunk bits")
+    ap.add_argument("--gather-pinned", type=int, default=4,
+                    help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()

@@ -195,7 +195,7 @@ void sv_options_default(sv_options *o) {
     o->chunk_bits = 13;
     o->reserve = 0;
     o->restore_layout = 1;
-    o->seg_bits = 5;
+    o->seg_bits = 4;
     o->use_tc = 0;
     o->use_model = 0;
     o->threads = 0;

@@ -25,6 +25,7 @@
 // error word and stops.
 #include <cuda.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -55,29 +56,79 @@ __device__ __forceinline__ void cmul_acc(T &yr, T &yi, T mr, T mi, T xr, T xi) {
     yi = fma(mi, xr, yi);
 }
 
+// ---- explicit shared-memory access with 32-bit shared addresses.  Chunk data goes through
+// volatile accesses (ordered with the barriers); the section program is read-only after the
+// kernel's first barrier, so its loads are pure and the compiler may reuse them across groups.
+template <typename T> struct SM;
+template <> struct SM<float> {
+    static __device__ __forceinline__ void ld(uint32_t a, float &x, float &y) {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+    }
+    static __device__ __forceinline__ void st(uint32_t a, float x, float y) {
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+    }
+    static __device__ __forceinline__ void ldc4(uint32_t a, float &x, float &y, float &z, float &w) {
+        asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+    }
+};
+template <> struct SM<double> {
+    static __device__ __forceinline__ void ld(uint32_t a, double &x, double &y) {
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+    }
+    static __device__ __forceinline__ void st(uint32_t a, double x, double y) {
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(x), "d"(y) : "memory");
+    }
+    static __device__ __forceinline__ void ldc4(uint32_t a, double &x, double &y, double &z, double &w) {
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(z), "=d"(w) : "r"(a + 16));
+    }
+};
+
+__device__ __forceinline__ int lds_s8(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int lds_s16(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void ldc_i4(uint32_t a, int &x, int &y, int &z, int &w) {
+    asm("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void load_mat(uint32_t a, T (&m)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; k += 4) SM<T>::ldc4(a + k * (uint32_t)sizeof(T), m[k], m[k + 1], m[k + 2], m[k + 3]);
+}
+
 template <typename T, int NA, int A>
-__device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
-    const T m0r = m[0], m0i = m[1], m1r = m[2], m1i = m[3], m2r = m[4], m2i = m[5], m3r = m[6], m3i = m[7];
+__device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T m[8];
+    load_mat<T, 8>(ma, m);
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
         if (x & (1 << A)) continue;
         const int y = x | (1 << A);
         const T ar = r[x], ai = i[x], br = r[y], bi = i[y];
         T pr = 0, pi = 0, qr = 0, qi = 0;
-        cmul_acc(pr, pi, m0r, m0i, ar, ai);
-        cmul_acc(pr, pi, m1r, m1i, br, bi);
-        cmul_acc(qr, qi, m2r, m2i, ar, ai);
-        cmul_acc(qr, qi, m3r, m3i, br, bi);
+        cmul_acc(pr, pi, m[0], m[1], ar, ai);
+        cmul_acc(pr, pi, m[2], m[3], br, bi);
+        cmul_acc(qr, qi, m[4], m[5], ar, ai);
+        cmul_acc(qr, qi, m[6], m[7], br, bi);
         r[x] = pr; i[x] = pi; r[y] = qr; i[y] = qi;
     }
 }
 
 template <typename T, int NA, int A>
-__device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
-    const T d0r = m[0], d0i = m[1], d1r = m[2], d1i = m[3];
+__device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T d[4];
+    load_mat<T, 4>(ma, d);
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
-        const T dr = (x & (1 << A)) ? d1r : d0r, di = (x & (1 << A)) ? d1i : d0i;
+        const T dr = (x & (1 << A)) ? d[2] : d[0], di = (x & (1 << A)) ? d[3] : d[1];
         const T xr = r[x], xi = i[x];
         r[x] = fma(dr, xr, -di * xi);
         i[x] = fma(dr, xi, di * xr);
@@ -85,10 +136,9 @@ __device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], const T *__rest
 }
 
 template <typename T, int NA, int A, int B>
-__device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
+__device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
     T mm[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) mm[k] = m[k];
+    load_mat<T, 32>(ma, mm);
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
         if (x & ((1 << A) | (1 << B))) continue;
@@ -108,10 +158,9 @@ __device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], const T *__res
 }
 
 template <typename T, int NA, int A, int B>
-__device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
+__device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
     T d[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) d[k] = m[k];
+    load_mat<T, 8>(ma, d);
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
         const int l = ((x >> A) & 1) | (((x >> B) & 1) << 1);
@@ -123,8 +172,10 @@ __device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], const T *__rest
 }
 
 template <typename T, int NA, int A, int B>
-__device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], const T *__restrict__ m) {
-    const int p0 = (int)m[0], p1 = (int)m[1], p2 = (int)m[2], p3 = (int)m[3];
+__device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T pm[4];
+    load_mat<T, 4>(ma, pm);
+    const int p0 = (int)pm[0], p1 = (int)pm[1], p2 = (int)pm[2], p3 = (int)pm[3];
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
         if (x & ((1 << A) | (1 << B))) continue;
@@ -144,20 +195,20 @@ __device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], const T *__rest
 
 // Dispatch a gate on the register bits (a, b) -- compile-time bit positions via templates.
 template <typename T, int R, int A>
-__device__ __forceinline__ void one(int op, T (&r)[1 << R], T (&i)[1 << R], const T *m) {
+__device__ __forceinline__ void one(int op, T (&r)[1 << R], T (&i)[1 << R], uint32_t m) {
     if (op == OP_DENSE1) ap_dense1<T, 1 << R, A>(r, i, m);
     else ap_diag1<T, 1 << R, A>(r, i, m);
 }
 
 template <typename T, int R, int A, int B>
-__device__ __forceinline__ void two(int op, T (&r)[1 << R], T (&i)[1 << R], const T *m) {
+__device__ __forceinline__ void two(int op, T (&r)[1 << R], T (&i)[1 << R], uint32_t m) {
     if (op == OP_DENSE2) ap_dense2<T, 1 << R, A, B>(r, i, m);
     else if (op == OP_DIAG2) ap_diag2<T, 1 << R, A, B>(r, i, m);
     else ap_perm2<T, 1 << R, A, B>(r, i, m);
 }
 
 template <typename T, int R>
-__device__ __forceinline__ void apply_gate(int op, int code, const T *m, T (&r)[1 << R], T (&i)[1 << R]) {
+__device__ __forceinline__ void apply_gate(int op, int code, uint32_t m, T (&r)[1 << R], T (&i)[1 << R]) {
     if (op == OP_DENSE1 || op == OP_DIAG1) {
         switch (code) {
             case 0: one<T, R, 0>(op, r, i, m); break;
@@ -184,64 +235,86 @@ __device__ __forceinline__ void apply_gate(int op, int code, const T *m, T (&r)[
     }
 }
 
-// One register group over the chunk in shared memory.
-template <typename T, int R, int NC>
-__device__ __forceinline__ void run_segment(typename V2<T>::type *buf, const DevSeg &sg,
-                                            const DevGate<T> *__restrict__ gates, int ctid, const int *swz,
+constexpr int kMaxRest = 8;  // chunk bits above the lanes per register group (c <= R + 5 + 8)
+
+// One register group over the chunk in shared memory.  `buf`, `seg` and `gates` are shared
+// addresses of the chunk buffer, the group descriptor and the section's gate records.  Each
+// thread handles KU groups at a time so that every gate matrix is read once for all of them.
+template <typename T, int R, int NC, int KU>
+__device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t gates, int ctid, const int *swz,
                                             int c) {
-    using T2 = typename V2<T>::type;
     constexpr int NA = 1 << R;
-    const int lane = ctid & 31, warp = ctid >> 5;
-    // addresses of the group's amplitudes relative to the group base, natural and swizzled
-    int off[NA], soff[NA];
-    {
-        int po[R], pf[R];
+    constexpr int SH = sizeof(T) == 4 ? 3 : 4;  // log2 bytes per amplitude
+    // descriptor (DevSeg layout: pos[8] lane[5] nrest flags r rest[16] g0 g1)
+    int po[R], pf[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            po[j] = 1 << sg.pos[j];
-            pf[j] = po[j] ^ swz[sg.pos[j]];
-        }
-#pragma unroll
-        for (int b = 0; b < NA; ++b) {
-            int o = 0, f = 0;
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
-            off[b] = o;
-            soff[b] = f;
-        }
+    for (int j = 0; j < R; ++j) {
+        const int p = lds_s8(seg + j);
+        po[j] = 1 << p;
+        pf[j] = po[j] ^ swz[p];
     }
+    const int lane = ctid & 31;
+    int lbase = 0, lfb = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int p = lds_s8(seg + 8 + j);
+        if ((lane >> j) & 1) { lbase |= 1 << p; lfb ^= swz[p]; }
+    }
+    const int nrest = lds_s8(seg + 13), flags = lds_s8(seg + 14);
+    int rpo[kMaxRest], rpf[kMaxRest];
+#pragma unroll
+    for (int j = 0; j < kMaxRest; ++j) {
+        const int p = j < nrest ? lds_s8(seg + 16 + j) : 0;
+        rpo[j] = j < nrest ? 1 << p : 0;
+        rpf[j] = j < nrest ? swz[p] : 0;
+    }
+    const int g0 = lds_s16(seg + 32), g1 = lds_s16(seg + 34);
     const int G = 1 << (c - R);
-    const int nrest = sg.nrest;
-    for (int g = ctid; g < G; g += NC) {
-        // group base: lane bits, then warp/iteration bits
-        int base = 0, fb = 0;
+
+    for (int gb = ctid; gb < G; gb += NC * KU) {
+        T re[KU][NA], im[KU][NA];
+        int base[KU], sbase[KU];
 #pragma unroll
-        for (int j = 0; j < 5; ++j)
-            if ((lane >> j) & 1) { base |= 1 << sg.lane[j]; fb ^= swz[sg.lane[j]]; }
-        const int hi = (g >> 5);
-        for (int j = 0; j < nrest; ++j)
-            if ((hi >> j) & 1) { base |= 1 << sg.rest[j]; fb ^= swz[sg.rest[j]]; }
-        (void)warp;
-        const int sbase = base ^ fb;
-        T re[NA], im[NA];
-        if (sg.flags & 1) {
+        for (int u = 0; u < KU; ++u) {
+            const int hi = (gb + u * NC) >> 5;
+            int bs = lbase, fb = lfb;
 #pragma unroll
-            for (int b = 0; b < NA; ++b) { const T2 v = buf[base | off[b]]; re[b] = v.x; im[b] = v.y; }
-        } else {
+            for (int j = 0; j < kMaxRest; ++j)
+                if ((hi >> j) & 1) { bs |= rpo[j]; fb ^= rpf[j]; }
+            base[u] = bs;
+            sbase[u] = bs ^ fb;
+            if (gb + u * NC < G) {
 #pragma unroll
-            for (int b = 0; b < NA; ++b) { const T2 v = buf[sbase ^ soff[b]]; re[b] = v.x; im[b] = v.y; }
+                for (int b = 0; b < NA; ++b) {
+                    int o = 0, f = 0;
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
+                    const int a = (flags & 1) ? (base[u] | o) : (sbase[u] ^ f);
+                    SM<T>::ld(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                }
+            }
         }
-        for (int gi = sg.g0; gi < sg.g1; ++gi) {
-            const DevGate<T> *gp = gates + gi;
-            apply_gate<T, R>(gp->op, gp->code, gp->m, re, im);
+        for (int gi = g0; gi < g1; ++gi) {
+            const uint32_t ga = gates + (uint32_t)gi * (uint32_t)sizeof(DevGate<T>);
+            int op, ra, rb, code;
+            ldc_i4(ga, op, ra, rb, code);
+#pragma unroll
+            for (int u = 0; u < KU; ++u) apply_gate<T, R>(op, code, ga + 16, re[u], im[u]);
         }
-        if (sg.flags & 2) {
 #pragma unroll
-            for (int b = 0; b < NA; ++b) { T2 v; v.x = re[b]; v.y = im[b]; buf[base | off[b]] = v; }
-        } else {
+        for (int u = 0; u < KU; ++u) {
+            if (gb + u * NC < G) {
 #pragma unroll
-            for (int b = 0; b < NA; ++b) { T2 v; v.x = re[b]; v.y = im[b]; buf[sbase ^ soff[b]] = v; }
+                for (int b = 0; b < NA; ++b) {
+                    int o = 0, f = 0;
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
+                    const int a = (flags & 2) ? (base[u] | o) : (sbase[u] ^ f);
+                    SM<T>::st(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                }
+            }
         }
     }
 }
@@ -268,8 +341,10 @@ __device__ __forceinline__ int64_t gather_origin(const GatherArgs &ga, int64_t j
     return x;
 }
 
-template <typename T, int R, int NC>
-__global__ void __launch_bounds__(NC + 32, 1)
+constexpr int CG = 2;  // consumer groups per CTA
+
+template <typename T, int R, int NC, int KU>
+__global__ void __launch_bounds__(CG * NC + 32, 1)
     k_block(typename V2<T>::type *__restrict__ state, int c, int64_t nchunks, int nbuf,
             const unsigned char *__restrict__ prog, int nseg, int ngate, int *err,
             const __grid_constant__ CUtensorMap tmap, const GatherArgs ga_in) {
@@ -344,21 +419,26 @@ __global__ void __launch_bounds__(NC + 32, 1)
     }
 
     // -------------------------------------------------------------- consumers
-    const int ctid = threadIdx.x - 32;
-    for (int64_t it = 0; it < count; ++it) {
+    // CG groups of NC threads take alternate chunks, so one group's shared-memory phases
+    // overlap another group's arithmetic; each group synchronises on its own named barrier.
+    const int cg = (threadIdx.x - 32) / NC;
+    const int ctid = (threadIdx.x - 32) % NC;
+    const int bar_id = 1 + cg;
+    for (int64_t it = cg; it < count; it += CG) {
         const int s = (int)(it % nbuf);
         const int64_t j = blockIdx.x + it * gridDim.x;
         if (!ptx::mbar_wait(&full[s], (uint32_t)((it / nbuf) & 1), kWaitLimitNs)) {
             atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
             *abort_flag = 1;
         }
-        ptx::named_bar_sync(1, NC);
+        ptx::named_bar_sync(bar_id, NC);
         if (*abort_flag) break;
         T2 *buf = bufs + (size_t)s * chunk_amps;
         for (int si = 0; si < nseg; ++si) {
-            run_segment<T, R, NC>(buf, segs[si], gates, ctid, swz, c);
+            run_segment<T, R, NC, KU>(ptx::smem_addr(buf), ptx::smem_addr(segs) + (uint32_t)(si * sizeof(DevSeg)),
+                                      ptx::smem_addr(gates), ctid, swz, c);
             if (si == nseg - 1) ptx::fence_proxy_async_smem();
-            ptx::named_bar_sync(1, NC);
+            ptx::named_bar_sync(bar_id, NC);
         }
         if (nseg == 0) ptx::fence_proxy_async_smem();
         if (ctid == 0) {
@@ -377,23 +457,18 @@ __global__ void __launch_bounds__(NC + 32, 1)
                 }
             }
             ptx::bulk_commit();
-            if (nbuf >= 3) {
-                // release the previous buffer once its write-back has read shared memory; the
-                // third buffer keeps a load in flight meanwhile
-                ptx::bulk_wait_read<1>();
-                if (it >= 1) ptx::mbar_arrive(&empty[(it - 1) % nbuf]);
-            } else {
-                ptx::bulk_wait_read<0>();
-                ptx::mbar_arrive(&empty[s]);
-            }
+            // release the buffer to the producer once the write-back has read it
+            ptx::bulk_wait_read<0>();
+            ptx::mbar_arrive(&empty[s]);
         }
     }
     if (ctid == 0) ptx::bulk_wait<0>();
 }
 
-template <typename T, int R, int NC>
+template <typename T, int R, int NC, int KU>
 void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st,
                   const CUtensorMap &tmap, const GatherArgs &ga) {
+    if (ce - R - 5 > kMaxRest) fail(SV_ERR_UNSUPPORTED, "chunk too wide for the register-group layout");
     using T2 = typename V2<T>::type;
     const size_t chunk_bytes = (size_t(1) << ce) * sizeof(T2);
     const int64_t nchunks = int64_t(1) << (n - ce);
@@ -405,24 +480,16 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     while (nbuf > 1 && nbuf * chunk_bytes + extra > max_smem) --nbuf;
     const size_t smem = nbuf * chunk_bytes + extra;
     if (smem > max_smem) fail(SV_ERR_UNSUPPORTED, "chunk and section program do not fit in shared memory");
-    auto kern = k_block<T, R, NC>;
+    auto kern = k_block<T, R, NC, KU>;
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(block)");
     int per_sm = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, smem), "occupancy(block)");
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CG * NC + 32, smem), "occupancy(block)");
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm);
-    kern<<<(unsigned)grid, NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
+    kern<<<(unsigned)grid, CG * NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
                                                 ngate, err, tmap, ga);
     check_cuda(cudaGetLastError(), "block kernel launch");
-}
-
-template <typename T, int R, int NC>
-void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st) {
-    CUtensorMap none;
-    std::memset(&none, 0, sizeof(none));
-    GatherArgs ga{};
-    launch_typed<T, R, NC>(state, n, ce, prog, nseg, ngate, err, st, none, ga);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -471,11 +538,25 @@ CUtensorMap make_gather_map(void *state, int n, const GatherLayout &lay, int ele
 
 size_t devgate_bytes(int dtype) { return dtype == SV_C64 ? sizeof(DevGate<float>) : sizeof(DevGate<double>); }
 
-int block_threads(int ce, int seg_bits) {
-    const int groups = 1 << (ce - seg_bits);
-    const int cap = seg_bits >= 5 ? 256 : 512;  // 2^5 amplitudes per thread: 256 threads fit the registers
-    const int nc = groups >= 512 ? 512 : (groups >= 256 ? 256 : 128);
-    return nc < cap ? nc : cap;
+// Threads per consumer group: 2^4-amplitude groups need ~96 registers (2 x 256 threads fit the
+// register file), 2^5-amplitude and complex128 groups ~170 (2 x 128 threads).
+// Threads per consumer group: complex64 with 2^4-amplitude register groups runs 2 x 256
+// consumers (17 warps, <= 96 registers a thread); 2^5-amplitude groups and complex128 run
+// 2 x 128 (9 warps, <= 168 registers).  Each thread holds one register group at a time.
+int block_threads(int ce, int seg_bits, int dtype) {
+    (void)ce;
+    return (dtype == SV_C64 && seg_bits == 4) ? 256 : 128;
+}
+
+static void dispatch(int dtype, int r, int nc, void *state, int n, int ce, const void *prog, int nseg, int ngates,
+                     int *err, cudaStream_t st, const CUtensorMap &m, const GatherArgs &ga) {
+    (void)nc;
+    if (dtype == SV_C64) {
+        if (r == 4) launch_typed<float, 4, 256, 1>(state, n, ce, prog, nseg, ngates, err, st, m, ga);
+        else launch_typed<float, 5, 128, 1>(state, n, ce, prog, nseg, ngates, err, st, m, ga);
+    } else {
+        launch_typed<double, 4, 128, 1>(state, n, ce, prog, nseg, ngates, err, st, m, ga);
+    }
 }
 
 void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, int nseg, int ngates, int *dev_err,
@@ -483,20 +564,10 @@ void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, in
     const int ce = c < n ? c : n;
     if (ce < 4) fail(SV_ERR_UNSUPPORTED, "blocked path needs a chunk of at least 4 bits");
     const int r = seg_bits < ce ? seg_bits : ce;  // the register groups were built with this width
-    const int nc = block_threads(ce, r);
-    if (dtype == SV_C64) {
-        if (r == 4) {
-            if (nc == 512) launch_typed<float, 4, 512>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-            else if (nc == 256) launch_typed<float, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-            else launch_typed<float, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-        } else {
-            if (nc == 256) launch_typed<float, 5, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-            else launch_typed<float, 5, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-        }
-    } else {
-        if (nc >= 256) launch_typed<double, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-        else launch_typed<double, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st);
-    }
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    dispatch(dtype, r, block_threads(ce, r, dtype), state, n, ce, dev_prog, nseg, ngates, dev_err, st, none,
+             GatherArgs{});
 }
 
 void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay, const void *dev_prog, int nseg,
@@ -510,21 +581,7 @@ void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay,
         fail(SV_ERR_UNSUPPORTED, "gathered chunk boxes smaller than 128 bytes (pin more low bits)");
     const CUtensorMap m = make_gather_map(state, n, lay, elem);
     const int r = seg_bits < ce ? seg_bits : ce;
-    const int nc = block_threads(ce, r);
-    const GatherArgs &ga = lay.args;
-    if (dtype == SV_C64) {
-        if (r == 4) {
-            if (nc == 512) launch_typed<float, 4, 512>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-            else if (nc == 256) launch_typed<float, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-            else launch_typed<float, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-        } else {
-            if (nc == 256) launch_typed<float, 5, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-            else launch_typed<float, 5, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-        }
-    } else {
-        if (nc >= 256) launch_typed<double, 4, 256>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-        else launch_typed<double, 4, 128>(state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, ga);
-    }
+    dispatch(dtype, r, block_threads(ce, r, dtype), state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, lay.args);
 }
 
 }  // namespace sv

@@ -49,7 +49,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     plan->c = c;
     plan->reserve = o.reserve;
     plan->restore = o.restore_layout ? 1 : 0;
-    plan->seg_bits = (o.seg_bits == 4 || o.seg_bits == 5) ? o.seg_bits : 5;
+    plan->seg_bits = (o.seg_bits == 4 || o.seg_bits == 5) ? o.seg_bits : 4;
     plan->use_tc = o.use_tc;
     plan->pinned = pinned;
     plan->keys.reserve((size_t)n_gates);

@@ -50,7 +50,7 @@ struct GateKey {
 }  // namespace sv
 
 struct sv_plan {
-    int32_t n = 0, c = 0, reserve = 0, restore = 1, seg_bits = 5, use_tc = 0, pinned = 0;
+    int32_t n = 0, c = 0, reserve = 0, restore = 1, seg_bits = 4, use_tc = 0, pinned = 0;
     std::vector<sv::PlanOp> ops;
     std::vector<int32_t> final_map;
     std::vector<sv::GateKey> keys;  // structure of the gate list it was made from
