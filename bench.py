@@ -266,7 +266,7 @@ def run_ours(args):
         w["c"] = args.chunk_bits
     n, c, desc = w["n"], w["c"], w["desc"]
     G = len(desc)
-    plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=args.gather_pinned)
+    plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=args.gather_pinned, use_tc=int(args.tc))
     stream = torch.cuda.Stream()
     st = sv.StateVector(n, "c64", stream=stream)
     st.set_profiling(True)
@@ -408,6 +408,7 @@ def main():
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--seg-bits", type=int, default=4, help="register-group width inside a chunk (4 or 5)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the workload's chunk bits")
+    ap.add_argument("--tc", type=int, default=0, help="1: fused register groups on the tensor cores (3xTF32)")
     ap.add_argument("--gather-pinned", type=int, default=4,
                     help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

@@ -74,7 +74,91 @@ struct BlockProg {
     size_t off;
     int nseg, ngate;
     GatherLayout lay;  // gathered sections only
+    int op_index = -1;
+    bool gathered = false;
 };
+
+// Tensor-core programs: every register group of a section becomes one fused unitary.  A
+// section whose B operands (8 KiB per group) would not fit next to the chunk ring in shared
+// memory is split into consecutive sweeps of at most kMaxTcSegs groups.  Appended after the
+// section programs: the composer's work list and the FP64 gate records it reads.
+constexpr int kMaxTcSegs = 11;
+
+static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::vector<unsigned char> &host,
+                              std::vector<BlockProg> &progs, size_t &cs_off, int &ncs, size_t &g_off) {
+    host.clear();
+    progs.clear();
+    auto align = [&](size_t a) {
+        while (host.size() % a) host.push_back(0);
+    };
+    std::vector<ComposeSeg> cs;
+    std::vector<DevGate<double>> dg;
+    for (size_t oi = 0; oi < plan->ops.size(); ++oi) {
+        const PlanOp &op0 = plan->ops[oi];
+        if (op0.kind != 2 && op0.kind != 4) continue;
+        int width = std::min(plan->c, plan->n);
+        GatherLayout lay{};
+        PlanOp local = op0;
+        if (op0.kind == 4) {
+            lay = gather_layout(op0.mask, plan->n, 8);
+            for (BlockGate &g : local.gates)
+                for (int j = 0; j < g.nq; ++j) g.phys[j] = lay.local_of[g.phys[j]];
+            width = lay.ce;
+        }
+        const std::vector<HostSeg> segs = segment_block(local.gates, width, 4, 8);
+        for (size_t p0 = 0; p0 < segs.size(); p0 += kMaxTcSegs) {
+            const size_t p1 = std::min(segs.size(), p0 + (size_t)kMaxTcSegs);
+            BlockProg bp{};
+            bp.lay = lay;
+            bp.gathered = op0.kind == 4;
+            bp.op_index = (int)oi;
+            align(256);
+            bp.off = host.size();
+            bp.nseg = (int)(p1 - p0);
+            bp.ngate = 0;
+            for (size_t k = p0; k < p1; ++k) {
+                const HostSeg &s = segs[k];
+                DevSeg d;
+                std::memset(&d, 0, sizeof(d));
+                d.r = (int8_t)s.r;
+                for (int q = 0; q < s.r; ++q) d.pos[q] = (int8_t)s.pos[q];
+                for (int q = 0; q < 5; ++q) d.lane[q] = (int8_t)s.lane[q];
+                d.nrest = (int8_t)s.nrest;
+                for (int q = 0; q < s.nrest; ++q) d.rest[q] = (int8_t)s.rest[q];
+                d.flags = (int8_t)((k == p0 ? 1 : 0) | (k + 1 == p1 ? 2 : 0));
+                const unsigned char *p = reinterpret_cast<const unsigned char *>(&d);
+                host.insert(host.end(), p, p + sizeof(d));
+            }
+            align(16);
+            const size_t b_base = host.size();
+            host.resize(host.size() + (size_t)bp.nseg * TC_B_BYTES, 0);
+            for (size_t k = p0; k < p1; ++k) {
+                ComposeSeg c{};
+                c.g0 = (int32_t)dg.size();
+                for (int32_t gi : segs[k].gates) {
+                    DevGate<double> g;
+                    const BlockGate &bg = local.gates[gi];
+                    encode_gate<double>(gates[bg.gi], bg, segs[k], g);
+                    dg.push_back(g);
+                }
+                c.g1 = (int32_t)dg.size();
+                c.b_off = (uint32_t)(b_base + (k - p0) * TC_B_BYTES);
+                cs.push_back(c);
+            }
+            progs.push_back(bp);
+        }
+    }
+    align(256);
+    cs_off = host.size();
+    ncs = (int)cs.size();
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(cs.data());
+    host.insert(host.end(), p, p + cs.size() * sizeof(ComposeSeg));
+    align(256);
+    g_off = host.size();
+    p = reinterpret_cast<const unsigned char *>(dg.data());
+    host.insert(host.end(), p, p + dg.size() * sizeof(DevGate<double>));
+    align(256);
+}
 
 template <typename T>
 static void build_programs(const sv_plan *plan, const sv_gate *gates, int seg_bits, std::vector<unsigned char> &host,
@@ -97,7 +181,9 @@ static void build_programs(const sv_plan *plan, const sv_gate *gates, int seg_bi
                 for (int j = 0; j < g.nq; ++j) g.phys[j] = bp.lay.local_of[g.phys[j]];
             width = bp.lay.ce;
             opp = &local;
+            bp.gathered = true;
         }
+        bp.op_index = (int)(&op0 - plan->ops.data());
         const PlanOp &op = *opp;
         std::vector<HostSeg> segs = segment_block(op.gates, width, seg_bits, (int)(2 * sizeof(T)));
         std::vector<DevSeg> dsegs;
@@ -406,23 +492,40 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         std::vector<unsigned char> host;
         std::vector<BlockProg> progs;
         const int seg_bits = h->dtype == SV_C64 ? plan->seg_bits : 4;
-        if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
+        // tensor cores: complex64 with chunks of at least 11 bits (128-row tiles of 4-bit groups)
+        const bool tc = plan->use_tc && h->dtype == SV_C64 && std::min(plan->c, plan->n) - plan->reserve >= 11;
+        size_t cs_off = 0, g_off = 0;
+        int ncs = 0;
+        if (tc) build_programs_tc(plan, gates, host, progs, cs_off, ncs, g_off);
+        else if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
         else build_programs<double>(plan, gates, seg_bits, host, progs);
         upload_program(h, host);
-        size_t bi = 0;
         const unsigned char *base = static_cast<const unsigned char *>(h->prog);
-        for (const PlanOp &op : plan->ops) {
+        if (tc) {  // fuse every register group into its B operand, in FP64 on the GPU
+            launch_compose(base + cs_off, ncs, base + g_off, h->prog, h->stream);
+            ++st.kernel_launches;
+        }
+        size_t bi = 0;
+        for (size_t oi = 0; oi < plan->ops.size(); ++oi) {
+            const PlanOp &op = plan->ops[oi];
             if (op.kind == 2 || op.kind == 4) {
-                const BlockProg &bp = progs[bi++];
-                mark_begin(h, 1);
-                if (op.kind == 2)
-                    launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
-                                 seg_bits, h->stream);
-                else
-                    launch_block_gather(h->dtype, h->amp, h->n, bp.lay, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
-                                        seg_bits, h->stream);
-                mark_end(h);
-                ++st.sweeps_block;
+                for (; bi < progs.size() && progs[bi].op_index == (int)oi; ++bi) {
+                    const BlockProg &bp = progs[bi];
+                    mark_begin(h, 1);
+                    if (tc)
+                        launch_block_tc(h->amp, h->n, plan->c, bp.gathered ? &bp.lay : nullptr, base + bp.off, bp.nseg,
+                                        h->dev_err, h->stream);
+                    else if (!bp.gathered)
+                        launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
+                                     seg_bits, h->stream);
+                    else
+                        launch_block_gather(h->dtype, h->amp, h->n, bp.lay, base + bp.off, bp.nseg, bp.ngate,
+                                            h->dev_err, seg_bits, h->stream);
+                    mark_end(h);
+                    ++st.sweeps_block;
+                    ++st.kernel_launches;
+                }
+                continue;
             } else {
                 mark_begin(h, 2);
                 launch_permute(h->dtype, h->amp, h->n, op.pairs, h->stream);

@@ -319,6 +319,140 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
     }
 }
 
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Tensor-core register group (complex64, 4 bits): the group's fused unitary, stored as the
+// real-embedded B operand (B_hi at `bhi`, B_lo at bhi + 4096), is applied on tiles of 128
+// register groups: every thread writes its group's 32 reals split into TF32 high and low parts
+// to its TMEM lane (A_hi, A_lo), one thread issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo
+// (3 x 4 MMAs, M = 128, N = K = 32, FP32 accumulation), and every thread reads its row of D back.
+// Two tiles are in flight per group; TMEM columns of tile buffer k: A_hi [tcol + 96k, +32),
+// A_lo [+32, +64), D [+64, +96); `mbar[k]` signals its MMAs' completion.
+template <int NC>
+__device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint32_t bhi, int ctid, const int *swz,
+                                               int c, uint32_t tcol, int bar_id, uint64_t *mbar, uint32_t (&phase)[2],
+                                               volatile int *abort_flag) {
+    constexpr int R = 4, NA = 16;
+    int po[R], pf[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int p = lds_s8(seg + j);
+        po[j] = 1 << p;
+        pf[j] = po[j] ^ swz[p];
+    }
+    const int lane = ctid & 31;
+    int lbase = 0, lfb = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int p = lds_s8(seg + 8 + j);
+        if ((lane >> j) & 1) { lbase |= 1 << p; lfb ^= swz[p]; }
+    }
+    const int nrest = lds_s8(seg + 13), flags = lds_s8(seg + 14);
+    int rpo[kMaxRest], rpf[kMaxRest];
+#pragma unroll
+    for (int j = 0; j < kMaxRest; ++j) {
+        const int p = j < nrest ? lds_s8(seg + 16 + j) : 0;
+        rpo[j] = j < nrest ? 1 << p : 0;
+        rpf[j] = j < nrest ? swz[p] : 0;
+    }
+    const int T = (1 << (c - R)) / NC;  // 128-row tiles per chunk
+    const uint32_t lane_off = (uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16;  // this thread's TMEM lane
+    constexpr uint32_t idesc = ptx::idesc_tf32(128, 32);
+
+    // group base (natural and swizzled) of this thread's row in tile t
+    auto row_base = [&](int t, int &base, int &sbase) {
+        const int hi = (t * NC + ctid) >> 5;
+        int bs = lbase, fb = lfb;
+#pragma unroll
+        for (int j = 0; j < kMaxRest; ++j)
+            if ((hi >> j) & 1) { bs |= rpo[j]; fb ^= rpf[j]; }
+        base = bs;
+        sbase = bs ^ fb;
+    };
+    // byte steps between the group's amplitudes in Gray-code order (the natural and the
+    // swizzled address are both linear in the group index over GF(2)), load and store side
+    uint32_t ld_step[R], st_step[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        ld_step[j] = (uint32_t)((flags & 1) ? po[j] : pf[j]) << 3;
+        st_step[j] = (uint32_t)((flags & 2) ? po[j] : pf[j]) << 3;
+    }
+    // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
+    // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
+    auto stage = [&](int t, int k, int &base, int &sbase) {
+        row_base(t, base, sbase);
+        uint32_t ahi[32], alo[32];
+        // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
+        // buffer base is only 1 KiB aligned, so it is added after the XOR walk, never XORed
+        uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            if (b) off ^= ld_step[__ffs(b) - 1];
+            const int gidx = b ^ (b >> 1);  // Gray code: this amplitude's local index
+            float xr, xi;
+            SM<float>::ld(buf + off, xr, xi);
+            ahi[2 * gidx] = __float_as_uint(xr);
+            ahi[2 * gidx + 1] = __float_as_uint(xi);
+            alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u));
+            alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u));
+        }
+        const uint32_t col = tcol + (uint32_t)k * 96;
+        ptx::tmem_st32(col + lane_off, ahi);
+        ptx::tmem_st32(col + 32 + lane_off, alo);
+        ptx::tmem_wait_st();
+        ptx::tc_fence_before();
+        ptx::named_bar_sync(bar_id, NC);  // every row of the tile is in TMEM
+        if (ctid == 0) {
+            ptx::tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, s > 0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 32 + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, 1);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 4096 + 256 * s, 128, 1024), idesc,
+                                 1);
+            ptx::mma_commit(&mbar[k]);
+        }
+    };
+    // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
+    auto finish = [&](int k, int base, int sbase) -> bool {
+        if (!ptx::mbar_wait(&mbar[k], phase[k], kWaitLimitNs)) *abort_flag = 1;
+        phase[k] ^= 1;
+        ptx::named_bar_sync(bar_id, NC);  // the whole group leaves together if a wait expired
+        if (*abort_flag) return false;
+        ptx::tc_fence_after();
+        uint32_t y[32];
+        ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
+        ptx::tmem_wait_ld();
+        uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            if (b) off ^= st_step[__ffs(b) - 1];
+            const int gidx = b ^ (b >> 1);
+            SM<float>::st(buf + off, __uint_as_float(y[2 * gidx]), __uint_as_float(y[2 * gidx + 1]));
+        }
+        return true;
+    };
+    // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
+    int pb, ps;
+    stage(0, 0, pb, ps);
+    for (int t = 1; t < T; ++t) {
+        int nb, ns;
+        stage(t, t & 1, nb, ns);
+        if (!finish((t - 1) & 1, pb, ps)) return false;
+        pb = nb;
+        ps = ns;
+    }
+    return finish((T - 1) & 1, pb, ps);
+}
+
 // Tensor coordinates of the box that holds amplitude index x (box bits of x are zero).
 template <typename T2>
 __device__ __forceinline__ void gather_coords(const GatherArgs &ga, int64_t x, int *coord) {
@@ -343,7 +477,7 @@ __device__ __forceinline__ int64_t gather_origin(const GatherArgs &ga, int64_t j
 
 constexpr int CG = 2;  // consumer groups per CTA
 
-template <typename T, int R, int NC, int KU>
+template <typename T, int R, int NC, int KU, bool TC>
 __global__ void __launch_bounds__(CG * NC + 32, 1)
     k_block(typename V2<T>::type *__restrict__ state, int c, int64_t nchunks, int nbuf,
             const unsigned char *__restrict__ prog, int nseg, int ngate, int *err,
@@ -355,16 +489,20 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     const int chunk_amps = 1 << c;
     const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
     T2 *bufs = reinterpret_cast<T2 *>(smem);
-    // block program copied into shared memory: segments then gates (16-byte aligned)
+    // block program copied into shared memory: register groups, then gate records (SIMT) or the
+    // groups' B operands (tensor cores), 16-byte aligned
     const int seg_bytes = (int)((nseg * sizeof(DevSeg) + 15) & ~size_t(15));
-    const int prog_bytes = seg_bytes + ngate * (int)sizeof(DevGate<T>);
+    const int prog_bytes = seg_bytes + (TC ? nseg * TC_B_BYTES : ngate * (int)sizeof(DevGate<T>));
     unsigned char *sprog = smem + (size_t)nbuf * chunk_bytes;
     const DevSeg *segs = reinterpret_cast<const DevSeg *>(sprog);
     const DevGate<T> *gates = reinterpret_cast<const DevGate<T> *>(sprog + seg_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(sprog + ((prog_bytes + 15) & ~15));
     uint64_t *empty = full + nbuf;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + nbuf);
+    uint64_t *mma_bar = empty + nbuf;  // two per consumer group (tensor-core path)
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(mma_bar + 2 * CG);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 2 * CG) + 1;
     __shared__ int swz[24];
+    constexpr uint32_t kTmemCols = 512;  // 2 tiles x 96 columns per consumer group
 
     for (int k = threadIdx.x * 16; k < prog_bytes; k += blockDim.x * 16)
         *reinterpret_cast<uint4 *>(sprog + k) = *reinterpret_cast<const uint4 *>(prog + k);
@@ -374,10 +512,18 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
+        for (int g = 0; g < 2 * CG; ++g) ptx::mbar_init(&mma_bar[g], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
+    if (TC && (threadIdx.x >> 5) == 1) ptx::tmem_alloc(ptx::smem_addr(tmem_slot), kTmemCols);
+    if (TC) {
+        ptx::fence_proxy_async_smem();  // B operands written by generic stores, read by the tensor cores
+        ptx::tc_fence_before();
+    }
     __syncthreads();
+    if (TC) ptx::tc_fence_after();
+    const uint32_t tmem_base = TC ? *tmem_slot : 0u;
 
     const int64_t count = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -424,6 +570,8 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     const int cg = (threadIdx.x - 32) / NC;
     const int ctid = (threadIdx.x - 32) % NC;
     const int bar_id = 1 + cg;
+    uint32_t mma_phase[2] = {0, 0};
+    bool failed = false;
     for (int64_t it = cg; it < count; it += CG) {
         const int s = (int)(it % nbuf);
         const int64_t j = blockIdx.x + it * gridDim.x;
@@ -435,10 +583,24 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
         if (*abort_flag) break;
         T2 *buf = bufs + (size_t)s * chunk_amps;
         for (int si = 0; si < nseg; ++si) {
-            run_segment<T, R, NC, KU>(ptx::smem_addr(buf), ptx::smem_addr(segs) + (uint32_t)(si * sizeof(DevSeg)),
-                                      ptx::smem_addr(gates), ctid, swz, c);
+            const uint32_t seg_addr = ptx::smem_addr(segs) + (uint32_t)(si * sizeof(DevSeg));
+            if constexpr (TC) {
+                if (!run_segment_tc<NC>(ptx::smem_addr(buf), seg_addr,
+                                        ptx::smem_addr(sprog + seg_bytes) + (uint32_t)(si * TC_B_BYTES), ctid, swz, c,
+                                        tmem_base + (uint32_t)(cg * 192), bar_id, &mma_bar[2 * cg], mma_phase,
+                                        abort_flag)) {
+                    failed = true;
+                    break;
+                }
+            } else {
+                run_segment<T, R, NC, KU>(ptx::smem_addr(buf), seg_addr, ptx::smem_addr(gates), ctid, swz, c);
+            }
             if (si == nseg - 1) ptx::fence_proxy_async_smem();
             ptx::named_bar_sync(bar_id, NC);
+        }
+        if (failed) {
+            atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+            break;
         }
         if (nseg == 0) ptx::fence_proxy_async_smem();
         if (ctid == 0) {
@@ -463,9 +625,18 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
         }
     }
     if (ctid == 0) ptx::bulk_wait<0>();
+    if constexpr (TC) {
+        // every consumer is done with tensor memory before the allocating warp frees it
+        ptx::tc_fence_before();
+        ptx::named_bar_sync(1 + CG, CG * NC);
+        if ((threadIdx.x >> 5) == 1) {
+            ptx::tc_fence_after();
+            ptx::tmem_dealloc(tmem_base, kTmemCols);
+        }
+    }
 }
 
-template <typename T, int R, int NC, int KU>
+template <typename T, int R, int NC, int KU, bool TC = false>
 void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st,
                   const CUtensorMap &tmap, const GatherArgs &ga) {
     if (ce - R - 5 > kMaxRest) fail(SV_ERR_UNSUPPORTED, "chunk too wide for the register-group layout");
@@ -473,19 +644,24 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     const size_t chunk_bytes = (size_t(1) << ce) * sizeof(T2);
     const int64_t nchunks = int64_t(1) << (n - ce);
     const size_t seg_bytes = (nseg * sizeof(DevSeg) + 15) & ~size_t(15);
-    const size_t prog_bytes = (seg_bytes + ngate * sizeof(DevGate<T>) + 15) & ~size_t(15);
-    const size_t extra = prog_bytes + 2 * 8 * 4 + 16;  // program + barriers + abort flag
+    const size_t prog_bytes =
+        (seg_bytes + (TC ? (size_t)nseg * TC_B_BYTES : ngate * sizeof(DevGate<T>)) + 15) & ~size_t(15);
+    const size_t extra = prog_bytes + 256;  // program + mbarriers, abort flag, TMEM address
     int nbuf = 3;
     const size_t max_smem = 227 * 1024 - 1024;  // minus the static swizzle table (1 KiB aligned)
     while (nbuf > 1 && nbuf * chunk_bytes + extra > max_smem) --nbuf;
-    const size_t smem = nbuf * chunk_bytes + extra;
+    size_t smem = nbuf * chunk_bytes + extra;
     if (smem > max_smem) fail(SV_ERR_UNSUPPORTED, "chunk and section program do not fit in shared memory");
-    auto kern = k_block<T, R, NC, KU>;
+    // a tensor-core CTA takes all of its SM's tensor memory: reserve over half the shared memory
+    // so that the scheduler never places two on one SM
+    if (TC && smem < 120 * 1024) smem = 120 * 1024;
+    auto kern = k_block<T, R, NC, KU, TC>;
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(block)");
     int per_sm = 0;
     check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CG * NC + 32, smem), "occupancy(block)");
     if (per_sm < 1) per_sm = 1;
+    if (TC) per_sm = 1;  // each CTA allocates all 512 tensor-memory columns of its SM
     const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm);
     kern<<<(unsigned)grid, CG * NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
                                                 ngate, err, tmap, ga);
@@ -582,6 +758,26 @@ void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay,
     const CUtensorMap m = make_gather_map(state, n, lay, elem);
     const int r = seg_bits < ce ? seg_bits : ce;
     dispatch(dtype, r, block_threads(ce, r, dtype), state, n, ce, dev_prog, nseg, ngates, dev_err, st, m, lay.args);
+}
+
+}  // namespace sv
+
+namespace sv {
+
+void launch_block_tc(void *state, int n, int c, const GatherLayout *lay, const void *dev_prog, int nseg, int *dev_err,
+                     cudaStream_t st) {
+    const int ce = lay ? lay->ce : (c < n ? c : n);
+    if (ce < 11) fail(SV_ERR_UNSUPPORTED, "tensor-core sections need chunks of at least 11 bits");
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    GatherArgs ga{};
+    if (lay) {
+        if ((size_t)lay->args.box_amps * 8 < 128)
+            fail(SV_ERR_UNSUPPORTED, "gathered chunk boxes smaller than 128 bytes (pin more low bits)");
+        m = make_gather_map(state, n, *lay, 8);
+        ga = lay->args;
+    }
+    launch_typed<float, 4, 128, 1, true>(state, n, ce, dev_prog, nseg, 0, dev_err, st, m, ga);
 }
 
 }  // namespace sv

@@ -1,0 +1,111 @@
+// Gate fusion for the tensor-core path: every register group of a blocking section becomes one
+// dense 2^4 x 2^4 complex unitary, composed in FP64 on the GPU, then written as the B operand of
+// a real GEMM in the tensor cores' canonical shared-memory layout, split into TF32 high and
+// low parts.
+//
+// Real embedding: a register group holds 16 amplitudes x_c, stored interleaved as the row
+// [re x_0, im x_0, re x_1, ...] (K = 32).  The fused unitary U maps it to y_r = sum_c U_rc x_c,
+// i.e. D = A B with
+//     B[2c][2r] = Re U_rc,  B[2c+1][2r] = -Im U_rc,  B[2c][2r+1] = Im U_rc,  B[2c+1][2r+1] = Re U_rc.
+// B (K = 32 rows x N = 32 columns) is stored K-major without swizzle: 8 x 16-byte core
+// matrices, element (k, n) at byte (n / 8) * 1024 + (k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4.
+// The high part is B rounded to TF32 (round to nearest), the low part the remainder, also
+// rounded to nearest TF32 (the tensor cores would otherwise truncate it, a one-sided error).
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t b_offset(int k, int n) {
+    return (uint32_t)((n >> 3) * 1024 + (k >> 2) * 128 + (n & 7) * 16 + (k & 3) * 4);
+}
+
+// One CTA per register group, thread j composes column j of U (U e_j through the group's gates).
+__global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate<double> *__restrict__ gates,
+                              unsigned char *__restrict__ prog) {
+    const ComposeSeg sg = segs[blockIdx.x];
+    const int j = threadIdx.x;  // 0..15
+    double vr[16], vi[16];
+    for (int b = 0; b < 16; ++b) { vr[b] = b == j ? 1.0 : 0.0; vi[b] = 0.0; }
+    for (int gi = sg.g0; gi < sg.g1; ++gi) {
+        const DevGate<double> &g = gates[gi];
+        const int a = g.a;
+        if (g.op == OP_DENSE1 || g.op == OP_DIAG1) {
+            for (int x = 0; x < 16; ++x) {
+                if (x & (1 << a)) continue;
+                const int y = x | (1 << a);
+                double m[8];
+                if (g.op == OP_DENSE1) {
+                    for (int k = 0; k < 8; ++k) m[k] = g.m[k];
+                } else {
+                    m[0] = g.m[0]; m[1] = g.m[1]; m[2] = 0; m[3] = 0;
+                    m[4] = 0; m[5] = 0; m[6] = g.m[2]; m[7] = g.m[3];
+                }
+                const double ar = vr[x], ai = vi[x], br = vr[y], bi = vi[y];
+                vr[x] = m[0] * ar - m[1] * ai + m[2] * br - m[3] * bi;
+                vi[x] = m[0] * ai + m[1] * ar + m[2] * bi + m[3] * br;
+                vr[y] = m[4] * ar - m[5] * ai + m[6] * br - m[7] * bi;
+                vi[y] = m[4] * ai + m[5] * ar + m[6] * bi + m[7] * br;
+            }
+        } else {
+            const int b = g.b;
+            double m[32];
+            for (int k = 0; k < 32; ++k) m[k] = 0.0;
+            if (g.op == OP_DENSE2) {
+                for (int k = 0; k < 32; ++k) m[k] = g.m[k];
+            } else if (g.op == OP_DIAG2) {
+                for (int r = 0; r < 4; ++r) { m[2 * (5 * r)] = g.m[2 * r]; m[2 * (5 * r) + 1] = g.m[2 * r + 1]; }
+            } else {  // permutation: row r takes column m[r]
+                for (int r = 0; r < 4; ++r) m[2 * (4 * r + (int)g.m[r])] = 1.0;
+            }
+            for (int x = 0; x < 16; ++x) {
+                if (x & ((1 << a) | (1 << b))) continue;
+                const int id[4] = {x, x | (1 << a), x | (1 << b), x | (1 << a) | (1 << b)};
+                double xr[4], xi[4];
+                for (int k = 0; k < 4; ++k) { xr[k] = vr[id[k]]; xi[k] = vi[id[k]]; }
+                for (int r = 0; r < 4; ++r) {
+                    double yr = 0, yi = 0;
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const double mr = m[2 * (4 * r + cc)], mi = m[2 * (4 * r + cc) + 1];
+                        yr += mr * xr[cc] - mi * xi[cc];
+                        yi += mr * xi[cc] + mi * xr[cc];
+                    }
+                    vr[id[r]] = yr;
+                    vi[id[r]] = yi;
+                }
+            }
+        }
+    }
+    // column j of U is (vr, vi); write B entries with input index c = j
+    unsigned char *bhi = prog + sg.b_off, *blo = bhi + 4096;
+    for (int r = 0; r < 16; ++r) {
+        const double ur = vr[r], ui = vi[r];
+        const double val[4] = {ur, -ui, ui, ur};       // (k, n) = (2j, 2r), (2j+1, 2r), (2j, 2r+1), (2j+1, 2r+1)
+        const int kk[4] = {2 * j, 2 * j + 1, 2 * j, 2 * j + 1};
+        const int nn[4] = {2 * r, 2 * r, 2 * r + 1, 2 * r + 1};
+        for (int e = 0; e < 4; ++e) {
+            const float f = (float)val[e];
+            const uint32_t hi = tf32_rna(f);
+            const uint32_t lo = tf32_rna((float)(val[e] - (double)__uint_as_float(hi)));
+            *reinterpret_cast<uint32_t *>(bhi + b_offset(kk[e], nn[e])) = hi;
+            *reinterpret_cast<uint32_t *>(blo + b_offset(kk[e], nn[e])) = lo;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st) {
+    if (nseg <= 0) return;
+    k_compose_f64<<<nseg, 16, 0, st>>>((const ComposeSeg *)dev_segs, (const DevGate<double> *)dev_gates,
+                                       (unsigned char *)dev_prog);
+    check_cuda(cudaGetLastError(), "compose kernel launch");
+}
+
+}  // namespace sv

@@ -138,6 +138,15 @@ struct GatherLayout {
 
 GatherLayout gather_layout(uint64_t mask, int n, int elem_bytes);
 
+// Tensor-core path: per register group, the gates to fuse and where its B operand goes.
+struct ComposeSeg {
+    int32_t g0, g1;   // gate range in the FP64 gate array
+    uint32_t b_off;   // byte offset of the group's B_hi (B_lo follows at +4096) in the program
+    int32_t pad;
+};
+constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
+void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st);
+
 // ------------------------------------------------------------------ kernels (launchers)
 struct Mat1 { float m[8]; };
 struct Mat2 { float m[32]; };
@@ -157,6 +166,10 @@ void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, in
 // tensor copies.
 void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay, const void *dev_prog, int nseg,
                          int ngates, int *dev_err, int seg_bits, cudaStream_t st);
+// Tensor-core blocking section (complex64, 4-bit register groups, B operands in the program);
+// `lay` null for a contiguous chunk of c bits.
+void launch_block_tc(void *state, int n, int c, const GatherLayout *lay, const void *dev_prog, int nseg, int *dev_err,
+                     cudaStream_t st);
 size_t devgate_bytes(int dtype);
 
 // readouts

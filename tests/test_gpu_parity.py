@@ -262,3 +262,31 @@ def test_chunk_larger_than_shared_memory_rejected(sv):
             with pytest.raises(sv.SVError) as e:
                 st.apply(gates, sv.Plan(n, gates, **opts))
             assert e.value.status == sv._lib.SV_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ tensor-core fused groups (3xTF32)
+
+@pytest.mark.parametrize("n,c,pinned", [(14, 11, 0), (16, 12, 0), (17, 13, 0), (16, 11, 4), (20, 13, 4), (13, 13, 0)])
+def test_tensor_core_fused_groups(sv, n, c, pinned):
+    desc = _mixed(n, 150, 500 + n + c) + cg.quantum_volume(n, 6, n + 2) + cg.qft(n)
+    ref = sim.simulate(n, desc, 9)
+    got = _run(sv, n, desc, "c64", basis=9, plan_opts=dict(chunk_bits=c, gather_pinned=pinned, use_tc=1))
+    assert_close(got, ref, "c64")
+
+
+def test_tensor_core_many_groups_per_section(sv):
+    # a single section with far more register groups than fit beside the chunk ring: split
+    # into several sweeps over the same chunks
+    n = 13
+    desc = cg.quantum_volume(n, 40, 3)
+    ref = sim.simulate(n, desc)
+    got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=13, use_tc=1))
+    assert_close(got, ref, "c64")
+
+
+def test_tensor_core_quantum_volume_24(sv):
+    n = 24
+    desc = cg.quantum_volume(n, 10, 19)
+    ref = sim.simulate(n, desc)
+    got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=13, gather_pinned=4, use_tc=1))
+    assert_close(got, ref, "c64")
