@@ -408,7 +408,7 @@ def main():
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--seg-bits", type=int, default=4, help="register-group width inside a chunk (4 or 5)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the workload's chunk bits")
-    ap.add_argument("--tc", type=int, default=0, help="1: fused register groups on the tensor cores (3xTF32)")
+    ap.add_argument("--tc", type=int, default=1, help="1: fused register groups on the tensor cores (3xTF32)")
     ap.add_argument("--gather-pinned", type=int, default=4,
                     help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

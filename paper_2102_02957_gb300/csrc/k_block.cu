@@ -383,7 +383,8 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     }
     // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
     // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
-    auto stage = [&](int t, int k, int &base, int &sbase) {
+    bool failed = false;
+    auto stage = [&](int t, int k, int &base, int &sbase) -> bool {
         row_base(t, base, sbase);
         uint32_t ahi[32], alo[32];
         // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
@@ -405,7 +406,9 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         ptx::tmem_st32(col + 32 + lane_off, alo);
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
-        ptx::named_bar_sync(bar_id, NC);  // every row of the tile is in TMEM
+        // every row of the tile is in TMEM; the barrier also tells the group whether any
+        // thread's wait for an earlier tile expired
+        if (ptx::named_bar_or(bar_id, NC, failed)) return false;
         if (ctid == 0) {
             ptx::tc_fence_after();
 #pragma unroll
@@ -420,13 +423,16 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
                                  1);
             ptx::mma_commit(&mbar[k]);
         }
+        return true;
     };
     // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
-    auto finish = [&](int k, int base, int sbase) -> bool {
-        if (!ptx::mbar_wait(&mbar[k], phase[k], kWaitLimitNs)) *abort_flag = 1;
+    // (after an expired wait the tile is garbage; the group stops at its next barrier)
+    auto finish = [&](int k, int base, int sbase) {
+        if (!ptx::mbar_wait(&mbar[k], phase[k], kWaitLimitNs)) {
+            failed = true;
+            *abort_flag = 1;
+        }
         phase[k] ^= 1;
-        ptx::named_bar_sync(bar_id, NC);  // the whole group leaves together if a wait expired
-        if (*abort_flag) return false;
         ptx::tc_fence_after();
         uint32_t y[32];
         ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
@@ -438,19 +444,19 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
             const int gidx = b ^ (b >> 1);
             SM<float>::st(buf + off, __uint_as_float(y[2 * gidx]), __uint_as_float(y[2 * gidx + 1]));
         }
-        return true;
     };
     // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
     int pb, ps;
-    stage(0, 0, pb, ps);
+    if (!stage(0, 0, pb, ps)) return false;
     for (int t = 1; t < T; ++t) {
         int nb, ns;
-        stage(t, t & 1, nb, ns);
-        if (!finish((t - 1) & 1, pb, ps)) return false;
+        if (!stage(t, t & 1, nb, ns)) return false;
+        finish((t - 1) & 1, pb, ps);
         pb = nb;
         ps = ns;
     }
-    return finish((T - 1) & 1, pb, ps);
+    finish((T - 1) & 1, pb, ps);
+    return !ptx::named_bar_or(bar_id, NC, failed);  // the group leaves together
 }
 
 // Tensor coordinates of the box that holds amplitude index x (box bits of x are zero).

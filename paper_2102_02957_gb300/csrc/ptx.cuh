@@ -149,6 +149,18 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Named barrier that also returns the OR of `flag` over the participating threads.
+__device__ __forceinline__ bool named_bar_or(int id, int count, bool flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // ---- tensor memory and 5th-generation tensor-core MMA (tcgen05), one CTA (cta_group::1)
 // Allocate `ncols` TMEM columns (power of two >= 32); the whole warp executes it; the TMEM base
 // address is written to shared memory at `dst`.
