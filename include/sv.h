@@ -172,6 +172,37 @@ sv_status sv_get_apply_stats(sv_handle h, sv_apply_stats *out);
 /* on != 0: record CUDA events around every kernel that sv_apply_circuit launches. */
 sv_status sv_set_profiling(sv_handle h, int32_t on);
 
+/* ------------------------------------------------------------------ batched execution */
+/* Many independent complex64 states (noisy trajectories, parameter sets -- the paper's "shots",
+ * Sec. IV.B) advanced by ONE persistent kernel launch.  Each state gets a gathered-chunk plan
+ * (sv_options.chunk_bits capped at 13, gather_pinned = 4); a state that fits one chunk runs its
+ * whole circuit in one shared-memory residency.  The launch drains a work queue of (state,
+ * section, chunk) items; a chunk waits (bounded) for the earlier sections of its own state.
+ * Constraints: every handle complex64, on the current device, n >= 6; gate lists without SWAP
+ * relabels.  The batch object owns the device-side plans and queue; the states stay owned by
+ * their handles.  All handles must share one CUDA stream, on which the work runs (SV_ERR_ARG
+ * otherwise); SV_ERR_UNSUPPORTED for complex128, n < 6 or a SWAP gate. */
+typedef struct sv_batch *sv_batch_h;
+sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate *const *gates,
+                          const int64_t *n_gates, const sv_options *opts, sv_batch_h *out);
+/* Launch the batch once (asynchronous).  use_graph != 0: the launch (counter reset + kernel) is
+ * captured once into a CUDA graph and replayed on later runs. */
+sv_status sv_batch_run(sv_batch_h batch, int32_t use_graph);
+/* Wait for the last run; SV_ERR_TIMEOUT if a bounded wait in the launch expired. */
+sv_status sv_batch_sync(sv_batch_h batch);
+/* Number of chunk work items and sections in the batch. */
+sv_status sv_batch_info(sv_batch_h batch, int64_t *work_items, int32_t *sections);
+sv_status sv_batch_free(sv_batch_h batch);
+
+/* ------------------------------------------------------------------ autotuning */
+/* Time candidate executions of this circuit on a scratch n-qubit state of `dtype` (chunk bits
+ * 11..13, register-group width 4/5, gathered or chunk_swap layout, tensor cores on/off for
+ * complex64) and write the fastest options to *best (its other fields are copied from *base).
+ * best_ms receives the measured milliseconds of one application with those options.  Allocates
+ * and frees its own scratch state; synchronises the device. */
+sv_status sv_autotune(int32_t n, int32_t dtype, const sv_gate *gates, int64_t n_gates, const sv_options *base,
+                      sv_options *best, double *best_ms);
+
 /* ------------------------------------------------------------------ readouts (FP64 accumulate) */
 /* Measurement probabilities |a_i|^2 (Sec. II.A) for all 2^n indices.  out: 2^n doubles,
  * on the device when out_on_device != 0, else on the host. */

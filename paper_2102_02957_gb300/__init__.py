@@ -184,3 +184,55 @@ class StateVector:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many complex64 states advanced by one persistent launch (sv_batch_*).  `states` are
+    StateVector objects, `gate_lists` one gate array per state; both must outlive the batch."""
+
+    def __init__(self, states, gate_lists, **opts):
+        if len(states) != len(gate_lists):
+            raise ValueError("one gate list per state")
+        self._h = ctypes.c_void_p()
+        self._states = list(states)
+        self._gates = [np.ascontiguousarray(g) for g in gate_lists]
+        cnt = len(self._states)
+        hs = (ctypes.c_void_p * cnt)(*[s._h.value for s in self._states])
+        gp = (ctypes.c_void_p * cnt)(*[g.ctypes.data for g in self._gates])
+        ng = (ctypes.c_int64 * cnt)(*[len(g) for g in self._gates])
+        o = options(**opts)
+        check(lib().sv_batch_create(cnt, hs, gp, ng, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def run(self, use_graph: bool = False):
+        check(lib().sv_batch_run(self._h, int(bool(use_graph))))
+
+    def synchronize(self):
+        check(lib().sv_batch_sync(self._h))
+
+    def info(self):
+        items, sections = ctypes.c_int64(), ctypes.c_int32()
+        check(lib().sv_batch_info(self._h, ctypes.byref(items), ctypes.byref(sections)))
+        return items.value, sections.value
+
+    def close(self):
+        if self._h:
+            lib().sv_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(n: int, gates: np.ndarray, dtype="c64", **base):
+    """sv_autotune: time candidate options for this circuit on a scratch state; returns
+    (options dict, milliseconds of one application)."""
+    b = options(**base)
+    best = sv_options()
+    ms = ctypes.c_double()
+    check(lib().sv_autotune(n, DTYPES[dtype], gates.ctypes.data, len(gates), ctypes.byref(b), ctypes.byref(best),
+                            ctypes.byref(ms)))
+    keys = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned")
+    return {k: getattr(best, k) for k in keys}, ms.value

@@ -77,6 +77,13 @@ _SIGS = {
     "sv_expval_pauli": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "sv_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "sv_expval_pauli_noalloc": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "sv_batch_create": (ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(sv_options), ctypes.POINTER(_VP)]),
+    "sv_batch_run": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "sv_batch_sync": (ctypes.c_int, [_VP]),
+    "sv_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "sv_batch_free": (ctypes.c_int, [_VP]),
+    "sv_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(sv_options),
+                                   ctypes.POINTER(sv_options), ctypes.POINTER(ctypes.c_double)]),
     "sv_last_error": (ctypes.c_char_p, []),
 }
 

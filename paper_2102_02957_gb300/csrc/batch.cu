@@ -1,0 +1,355 @@
+// Batched execution (host side) and the autotuner.
+#include <algorithm>
+#include <cstring>
+
+#include "sv_internal.h"
+
+struct sv_batch {
+    int count = 0;
+    cudaStream_t stream = nullptr;  // the states' stream
+    cudaStream_t work = nullptr;    // the batch's own stream (capturable; joined to `stream`)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int device = 0;
+    unsigned char *dev = nullptr;  // one allocation: ops, programs, state pointers, counters
+    size_t off_ops = 0, off_progs = 0, off_amps = 0, off_counters = 0, counters_bytes = 0;
+    int nops = 0;
+    int64_t total = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~sv_batch() {
+        if (work) cudaStreamSynchronize(work);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (work) cudaStreamDestroy(work);
+        if (dev) cudaFree(dev);
+    }
+};
+
+namespace sv {
+namespace {
+
+void launch_once(sv_batch *b) {
+    unsigned char *c = b->dev + b->off_counters;
+    check_cuda(cudaMemsetAsync(c, 0, b->counters_bytes, b->work), "cudaMemsetAsync(batch counters)");
+    int *ops_done = reinterpret_cast<int *>(c);
+    int *chunks_done = ops_done + b->count;
+    unsigned long long *next = reinterpret_cast<unsigned long long *>(c + (((size_t)(b->count + b->nops) * 4 + 15) & ~size_t(15)));
+    int *err = reinterpret_cast<int *>(next + 1);
+    launch_batch(b->dev + b->off_ops, b->nops, b->dev + b->off_progs,
+                 reinterpret_cast<void *const *>(b->dev + b->off_amps), ops_done, chunks_done, next, b->total, err,
+                 b->work);
+}
+
+int *batch_err(sv_batch *b) {
+    unsigned char *c = b->dev + b->off_counters;
+    unsigned long long *next = reinterpret_cast<unsigned long long *>(c + (((size_t)(b->count + b->nops) * 4 + 15) & ~size_t(15)));
+    return reinterpret_cast<int *>(next + 1);
+}
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+#define SV_API_BEGIN try {
+#define SV_API_END                 \
+    return SV_OK;                  \
+    }                              \
+    catch (const sv::Error &e) {   \
+        sv::set_error(e.msg);      \
+        return e.code;             \
+    }                              \
+    catch (const std::bad_alloc &) { \
+        sv::set_error("host allocation failed"); \
+        return SV_ERR_OOM;         \
+    }                              \
+    catch (...) {                  \
+        sv::set_error("unexpected exception"); \
+        return SV_ERR_CUDA;        \
+    }
+
+extern "C" {
+
+sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate *const *gates, const int64_t *n_gates,
+                          const sv_options *opts, sv_batch_h *out) {
+    SV_API_BEGIN
+    if (!out || count <= 0 || !states || !gates || !n_gates) fail(SV_ERR_ARG, "sv_batch_create: bad arguments");
+    *out = nullptr;
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    std::unique_ptr<sv_batch> b(new sv_batch());
+    b->count = count;
+    b->stream = states[0]->stream;
+    b->device = dev;
+
+    sv_options base;
+    if (opts) base = *opts; else sv_options_default(&base);
+    std::vector<std::vector<BatchOp>> per_state((size_t)count);
+    std::vector<unsigned char> progs;
+    auto align = [&](size_t a) {
+        while (progs.size() % a) progs.push_back(0);
+    };
+    for (int s = 0; s < count; ++s) {
+        const sv_state *h = states[s];
+        if (!h) fail(SV_ERR_ARG, "sv_batch_create: null state");
+        if (h->dtype != SV_C64) fail(SV_ERR_UNSUPPORTED, "sv_batch_create: batched states are complex64");
+        if (h->device != dev) fail(SV_ERR_ARG, "sv_batch_create: state on another device");
+        if (h->n < 6) fail(SV_ERR_UNSUPPORTED, "sv_batch_create: states need at least 6 qubits");
+        if (h->stream != b->stream) fail(SV_ERR_ARG, "sv_batch_create: all states must use one stream");
+        sv_options o = base;
+        o.chunk_bits = std::min(std::max(o.chunk_bits, 6), kBatchMaxChunkBits);
+        o.gather_pinned = std::min(4, std::min(o.chunk_bits, h->n) - 2);
+        o.reserve = 0;
+        o.seg_bits = 4;
+        o.use_tc = 0;
+        std::unique_ptr<sv_plan> plan(plan_blocking(h->n, gates[s], n_gates[s], o));
+        int opno = 0;
+        for (const PlanOp &op : plan->ops) {
+            if (op.kind == 1 || op.kind == 3) fail(SV_ERR_UNSUPPORTED, "sv_batch_create: SWAP relabels are not batched");
+            // chunk-local order: contiguous low run, then the other chunk bits ascending
+            const int n = h->n;
+            const uint64_t mask = op.kind == 4 ? op.mask : ((uint64_t(1) << std::min(plan->c, n)) - 1);
+            int low = 0;
+            while (low < n && ((mask >> low) & 1)) ++low;
+            std::vector<int> local_of(n, -1);
+            BatchOp bo{};
+            bo.state = s;
+            bo.low = low;
+            int k = 0;
+            for (int q = 0; q < n; ++q) {
+                if ((mask >> q) & 1) {
+                    if (q >= low) bo.high[bo.nhigh++] = (int8_t)q;
+                    local_of[q] = k++;
+                } else {
+                    bo.outer[bo.nouter++] = (int8_t)q;
+                }
+            }
+            bo.ce = k;
+            bo.nchunks = int64_t(1) << (n - k);
+            std::vector<BlockGate> loc = op.gates;
+            for (BlockGate &g : loc)
+                for (int j = 0; j < g.nq; ++j) g.phys[j] = local_of[g.phys[j]];
+            // a register group with many gates continues in further groups on the same bits
+            std::vector<HostSeg> segs;
+            for (HostSeg &sg : segment_block(loc, k, 4, 8)) {
+                constexpr size_t kMaxGatesPerGroup = 96;
+                for (size_t g0 = 0; g0 < std::max<size_t>(sg.gates.size(), 1); g0 += kMaxGatesPerGroup) {
+                    HostSeg part = sg;
+                    const size_t g1 = std::min(sg.gates.size(), g0 + kMaxGatesPerGroup);
+                    part.gates.assign(sg.gates.begin() + (ptrdiff_t)g0, sg.gates.begin() + (ptrdiff_t)g1);
+                    segs.push_back(std::move(part));
+                }
+            }
+            // programs of at most kBatchMaxProgBytes: long sections become consecutive sweeps
+            size_t p0 = 0;
+            while (p0 < segs.size()) {
+                size_t p1 = p0, gates_in = 0;
+                while (p1 < segs.size()) {
+                    const size_t g_next = gates_in + segs[p1].gates.size();
+                    const size_t bytes = ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + g_next * sizeof(DevGate<float>);
+                    if (bytes > (size_t)kBatchMaxProgBytes && p1 > p0) break;
+                    if (bytes > (size_t)kBatchMaxProgBytes) fail(SV_ERR_UNSUPPORTED, "register group too large");
+                    gates_in = g_next;
+                    ++p1;
+                }
+                std::vector<DevSeg> ds;
+                std::vector<DevGate<float>> dg;
+                for (size_t q = p0; q < p1; ++q) {
+                    DevSeg d;
+                    std::memset(&d, 0, sizeof(d));
+                    d.r = (int8_t)segs[q].r;
+                    for (int t = 0; t < segs[q].r; ++t) d.pos[t] = (int8_t)segs[q].pos[t];
+                    d.g0 = (int16_t)dg.size();
+                    for (int32_t gi : segs[q].gates) {
+                        DevGate<float> g;
+                        encode_gate<float>(gates[s][loc[gi].gi], loc[gi], segs[q], g);
+                        dg.push_back(g);
+                    }
+                    d.g1 = (int16_t)dg.size();
+                    ds.push_back(d);
+                }
+                align(256);
+                BatchOp piece = bo;
+                piece.op = opno++;
+                piece.prog_off = (uint32_t)progs.size();
+                piece.nseg = (int)ds.size();
+                piece.ngate = (int)dg.size();
+                const unsigned char *p = reinterpret_cast<const unsigned char *>(ds.data());
+                progs.insert(progs.end(), p, p + ds.size() * sizeof(DevSeg));
+                align(16);
+                p = reinterpret_cast<const unsigned char *>(dg.data());
+                progs.insert(progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
+                align(16);
+                piece.prog_bytes = (uint32_t)(progs.size() - piece.prog_off);
+                per_state[(size_t)s].push_back(piece);
+                p0 = p1;
+            }
+        }
+    }
+    // queue order: section level by section level, round-robin over the states
+    std::vector<BatchOp> ops;
+    size_t level = 0;
+    bool any = true;
+    int64_t total = 0;
+    while (any) {
+        any = false;
+        for (int s = 0; s < count; ++s) {
+            if (level < per_state[(size_t)s].size()) {
+                BatchOp o = per_state[(size_t)s][level];
+                o.first = total;
+                total += o.nchunks;
+                ops.push_back(o);
+                any = true;
+            }
+        }
+        ++level;
+    }
+    b->nops = (int)ops.size();
+    b->total = total;
+    // device layout
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    b->off_ops = place(ops.size() * sizeof(BatchOp));
+    b->off_progs = place(progs.size());
+    b->off_amps = place((size_t)count * sizeof(void *));
+    b->counters_bytes = (((size_t)(count + b->nops) * 4 + 15) & ~size_t(15)) + 16;
+    b->off_counters = place(b->counters_bytes);
+    check_cuda(cudaMalloc(&b->dev, off), "cudaMalloc(batch)");
+    check_cuda(cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking), "cudaStreamCreate(batch)");
+    check_cuda(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate(batch)");
+    check_cuda(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "cudaEventCreate(batch)");
+    std::vector<void *> amps((size_t)count);
+    for (int s = 0; s < count; ++s) amps[(size_t)s] = states[s]->amp;
+    check_cuda(cudaMemcpy(b->dev + b->off_ops, ops.data(), ops.size() * sizeof(BatchOp), cudaMemcpyHostToDevice), "H2D");
+    if (!progs.empty())
+        check_cuda(cudaMemcpy(b->dev + b->off_progs, progs.data(), progs.size(), cudaMemcpyHostToDevice), "H2D");
+    check_cuda(cudaMemcpy(b->dev + b->off_amps, amps.data(), amps.size() * sizeof(void *), cudaMemcpyHostToDevice), "H2D");
+    *out = b.release();
+    SV_API_END
+}
+
+sv_status sv_batch_run(sv_batch_h b, int32_t use_graph) {
+    SV_API_BEGIN
+    if (!b) fail(SV_ERR_ARG, "null batch");
+    // the batch's stream follows the states' stream, and the states' stream follows the batch
+    check_cuda(cudaEventRecord(b->ev_in, b->stream), "cudaEventRecord");
+    check_cuda(cudaStreamWaitEvent(b->work, b->ev_in, 0), "cudaStreamWaitEvent");
+    if (!use_graph) {
+        launch_once(b);
+    } else {
+        if (!b->exec) {
+            check_cuda(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            try {
+                launch_once(b);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(b->work, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            check_cuda(cudaStreamEndCapture(b->work, &b->graph), "cudaStreamEndCapture");
+            check_cuda(cudaGraphInstantiate(&b->exec, b->graph, 0), "cudaGraphInstantiate");
+        }
+        check_cuda(cudaGraphLaunch(b->exec, b->work), "cudaGraphLaunch");
+    }
+    check_cuda(cudaEventRecord(b->ev_out, b->work), "cudaEventRecord");
+    check_cuda(cudaStreamWaitEvent(b->stream, b->ev_out, 0), "cudaStreamWaitEvent");
+    SV_API_END
+}
+
+sv_status sv_batch_sync(sv_batch_h b) {
+    SV_API_BEGIN
+    if (!b) fail(SV_ERR_ARG, "null batch");
+    int e = 0;
+    check_cuda(cudaMemcpyAsync(&e, batch_err(b), sizeof(int), cudaMemcpyDeviceToHost, b->work), "read error word");
+    check_cuda(cudaStreamSynchronize(b->work), "cudaStreamSynchronize");
+    if (e == DEV_ERR_TIMEOUT) fail(SV_ERR_TIMEOUT, "a bounded device wait in the batch expired");
+    if (e != DEV_OK) fail(SV_ERR_CUDA, "batch error word set");
+    SV_API_END
+}
+
+sv_status sv_batch_info(sv_batch_h b, int64_t *items, int32_t *sections) {
+    SV_API_BEGIN
+    if (!b) fail(SV_ERR_ARG, "null batch");
+    if (items) *items = b->total;
+    if (sections) *sections = b->nops;
+    SV_API_END
+}
+
+sv_status sv_batch_free(sv_batch_h b) {
+    SV_API_BEGIN
+    delete b;
+    SV_API_END
+}
+
+sv_status sv_autotune(int32_t n, int32_t dtype, const sv_gate *gates, int64_t n_gates, const sv_options *base,
+                      sv_options *best, double *best_ms) {
+    SV_API_BEGIN
+    if (!best || (!gates && n_gates)) fail(SV_ERR_ARG, "sv_autotune: null argument");
+    sv_options b0;
+    if (base) b0 = *base; else sv_options_default(&b0);
+    sv_handle h = nullptr;
+    sv_status st = sv_create(n, dtype, nullptr, 0, nullptr, &h);
+    if (st != SV_OK) return st;
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    double best_t = 1e300;
+    sv_options best_o = b0;
+    const int cmax = std::min(n, 13);
+    try {
+        for (int c = std::max(std::min(n, 11), std::min(cmax, 6)); c <= cmax; ++c)
+            for (int seg : {4, 5})
+                for (int pin : {0, 4})
+                    for (int tc : {0, 1}) {
+                        if (dtype != SV_C64 && (seg == 5 || tc)) continue;
+                        if (tc && seg != 4) continue;
+                        if (pin && c - pin < 2) continue;
+                        sv_options o = b0;
+                        o.chunk_bits = c;
+                        o.seg_bits = seg;
+                        o.gather_pinned = pin;
+                        o.use_tc = tc;
+                        sv_plan_h p = nullptr;
+                        if (sv_plan_blocking(n, gates, n_gates, &o, &p) != SV_OK) continue;
+                        double ms = 1e300;
+                        if (sv_init_basis(h, 0) == SV_OK && sv_apply_circuit(h, gates, n_gates, p) == SV_OK &&
+                            sv_synchronize(h) == SV_OK) {
+                            check_cuda(cudaEventRecord(e0, h->stream), "cudaEventRecord");
+                            const sv_status a = sv_apply_circuit(h, gates, n_gates, p);
+                            check_cuda(cudaEventRecord(e1, h->stream), "cudaEventRecord");
+                            if (a == SV_OK && sv_synchronize(h) == SV_OK) {
+                                float t = 0;
+                                check_cuda(cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime");
+                                ms = t;
+                            }
+                        }
+                        sv_plan_free(p);
+                        if (ms < best_t) {
+                            best_t = ms;
+                            best_o = o;
+                        }
+                    }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        sv_destroy(h);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sv_destroy(h);
+    if (best_t >= 1e300) fail(SV_ERR_UNSUPPORTED, "sv_autotune: no candidate ran");
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
+    SV_API_END
+}
+
+}  // extern "C"

@@ -145,6 +145,23 @@ struct ComposeSeg {
     int32_t pad;
 };
 constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
+
+// Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
+// k < low (the contiguous low run of the chunk) and high[k - low] above it; the chunk index
+// enumerates the state bits outside the chunk, outer[] ascending.
+struct BatchOp {
+    int32_t state, op, ce, low;
+    int64_t nchunks, first;  // chunks of this section; first global work-item index
+    uint32_t prog_off, prog_bytes;
+    int32_t nseg, ngate;
+    int32_t nhigh, nouter;
+    int8_t high[24];
+    int8_t outer[40];
+};
+constexpr int kBatchMaxChunkBits = 13;
+constexpr int kBatchMaxProgBytes = 24 * 1024;
+void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
+                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int *dev_err, cudaStream_t st);
 void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernels (launchers)
