@@ -195,6 +195,35 @@ def run_reference(args):
     return 0
 
 
+def run_reference_batch(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import circuitgen as cg
+    ns, descs = cg.build_batch(args.workload)
+    budget = max(1.0, min(20.0, args.cpu_budget / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_batch_rate(ns, descs, budget)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, cores, sample = cpu_oracle_batch_rate(ns, descs, budget)
+        rates.append(rate)
+    dt = time.perf_counter() - t0
+    rate = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": rate, "unit": "state-gates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": rate, "unit": "state-gates/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": "state-gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _config(w):
     return {"workload": f"{args_workload_name(w)}", "n": w["n"], "gates": len(w["desc"]), "chunk_bits": w["c"],
             "state": "complex64", "l2": "state 8 GiB >> 129 MB L2 (no flush needed)"}
@@ -245,6 +274,159 @@ def _per_gate(sv, st, desc, stream, args, sweep_bytes):
                 "effective_GBs": G * sweep_bytes / (pg_ms / 1000.0) / 1e9,
                 "kernel_GBs": G * sweep_bytes / (s.ms_gate / 1000.0) / 1e9 if s.ms_gate else None}
     return per_gate, pg_ms
+
+
+# ------------------------------------------------------------------ batched workload
+BATCH_METRIC = "state-gates/s (batched persistent launch), 512 noisy trajectories n=12..24 + 64 HEA(20) sets, complex64"
+
+
+def cpu_oracle_batch_rate(ns, descs, budget_s: float):
+    """Oracle state-gates/s on the whole batch, extrapolated from a bounded sample: for each
+    distinct qubit count, gates of one of its circuits are applied one by one for an equal
+    share of `budget_s`; the workload time is sum over states of gates x seconds-per-gate(n)."""
+    from oracle import sim
+    sizes = sorted(set(ns))
+    per_gate_s = {}
+    share = budget_s / len(sizes)
+    for n in sizes:
+        d = descs[ns.index(n)]
+        st = sim.basis_state(n, 0)
+        done = 0
+        t0 = time.perf_counter()
+        for g in d:
+            sim.apply(st, n, [g])
+            done += 1
+            if time.perf_counter() - t0 > share:
+                break
+        per_gate_s[n] = (time.perf_counter() - t0) / max(1, done)
+    est = sum(len(d) * per_gate_s[n] for n, d in zip(ns, descs))
+    total = sum(len(d) for d in descs)
+    sample = (f"per qubit count {sizes[0]}..{sizes[-1]}: the first gates of one circuit in complex128 for "
+              f"{share:.2f} s each; whole-batch time extrapolated as sum(gates x s/gate(n)) = {est:.1f} s")
+    return total / est, sim.num_threads(), sample
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import circuitgen as cg
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    bar = _Barrier(world, torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    bar.barrier()
+    import paper_2102_02957_gb300 as sv
+
+    ns, descs = cg.build_batch(args.workload)
+    G = sum(len(d) for d in descs)
+    gates = [sv.make_gates(d) for d in descs]
+    stream = torch.cuda.Stream()
+    states = [sv.StateVector(n, "c64", stream=stream) for n in ns]
+    base = {} if not args.chunk_bits else dict(chunk_bits=args.chunk_bits)
+    if args.chunk_bits:
+        best, tune_ms = dict(chunk_bits=args.chunk_bits), None
+    else:
+        best, tune_ms = sv.batch_tune(states, gates, **base)
+    b = sv.Batch(states, gates, **best)
+    items, sections, nbytes = b.info()
+
+    def step():
+        b.run(use_graph=True, from_zero=True)
+
+    for _ in range(args.warmup):
+        step()
+    b.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    bar.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    b.synchronize()
+    torch.cuda.synchronize()
+    bar.barrier()
+    ck = clocks.stop()
+    elapsed_ms = bar.max(e0.elapsed_time(e1))
+    ms_step = elapsed_ms / args.steps
+    value = world * G * args.steps / (elapsed_ms / 1000.0)
+    peak, peak_kind = _peaks()
+    achieved = nbytes / (ms_step / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": _traffic_for("paper_2102_02957_gb300/csrc/k_batch.cu", args.workload),
+                "algorithmic_bytes_per_launch": nbytes, "launch_ms": ms_step}
+    norms = [s.norm2() for s in states[:: max(1, len(states) // 16)]]
+
+    # the same circuits one state after another on the single-state blocked path
+    seq_ms = None
+    if not args.no_per_gate:
+        plans = [sv.Plan(n, g, chunk_bits=13, gather_pinned=4) for n, g in zip(ns, gates)]
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for st, g, p in zip(states, gates, plans):
+            st.init_basis(0)
+            st.apply(g, p)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = s0.elapsed_time(s1)
+
+    # end to end through the public API: gate records on the host in, batch built (plan + program
+    # upload), run, every state's norm read back
+    e2e = None
+    if not args.no_e2e:
+        def e2e_step():
+            bb = sv.Batch(states, gates, **best)
+            bb.run(use_graph=False, from_zero=True)
+            out = [s.norm2() for s in states]
+            bb.close()
+            return out
+        e2e_step()
+        k2 = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        bar.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        dt = bar.max(time.perf_counter() - t0)
+        e2e = {"value": world * G * k2 / dt, "unit": "state-gates/s",
+               "h2d_bytes_per_step": int(sum(g.nbytes for g in gates)), "d2h_bytes_per_step": 8 * len(states),
+               "ms_per_step": 1000 * dt / k2}
+
+    b.close()
+    for st in states:
+        st.close()
+    torch.cuda.synchronize()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_batch_rate(ns, descs, args.cpu_budget)
+        cpu = {"value": rate, "unit": "state-gates/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": "state-gates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {len(ns)} states, n={min(ns)}..{max(ns)}, {G} gates, "
+                                   f"{sum(2 ** n for n in ns) * 8 / 2 ** 30:.1f} GiB complex64",
+                       "chunk_bits": best.get("chunk_bits"), "tuned_ms": tune_ms, "work_items": items,
+                       "sections": sections, "graph": True, "from_zero": True,
+                       "l2": "10 GiB of states >> 129 MB L2 (no flush needed)"},
+            "roofline": roofline, "sequential_blocked_ms": seq_ms,
+            "speedup_vs_sequential": (seq_ms / ms_step) if seq_ms else None,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": 1, "norms_sampled": norms,
+        }
+        print(json.dumps(line), flush=True)
+    bar.close()
+    return 0
 
 
 # ------------------------------------------------------------------ main GPU benchmark
@@ -414,9 +596,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()
+    import circuitgen as cg
+    batched = args.workload in cg.BATCH_WORKLOADS
     if args.impl == "reference":
-        return run_reference(args)
-    return run_ours(args)
+        return run_reference_batch(args) if batched else run_reference(args)
+    return run_batch(args) if batched else run_ours(args)
 
 
 if __name__ == "__main__":

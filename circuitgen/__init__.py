@@ -203,3 +203,24 @@ def build(name: str):
     if w["kind"] == "quantum_volume":
         return quantum_volume(w["n"], w["depth"], w["seed"])
     raise ValueError(name)
+
+
+# Batched workloads: many independent states (noisy trajectories plus ansatz parameter sets).
+BATCH_WORKLOADS = {
+    "traj512": dict(count=512, lo=12, hi=24, depth=30, p=1e-3, seed=8, hea_n=20, hea_sets=64, hea_layers=10),
+    # a smaller mix (about 0.5 GiB, above L2) for profiling and quick checks
+    "traj64": dict(count=64, lo=14, hi=22, depth=30, p=1e-3, seed=8, hea_n=20, hea_sets=8, hea_layers=10),
+}
+
+
+def build_batch(name: str):
+    """(qubit counts, gate lists) of a named batched workload: `count` depolarizing trajectories of
+    the random-layer circuit with qubit counts uniform in [lo, hi], then `hea_sets` parameter sets
+    of the hardware-efficient ansatz on hea_n qubits."""
+    w = BATCH_WORKLOADS[name]
+    ns = trajectory_sizes(w["count"], w["lo"], w["hi"], w["seed"])
+    descs = [noisy_trajectory(n, w["depth"], w["p"], w["seed"], t) for t, n in enumerate(ns)]
+    for k in range(w["hea_sets"]):
+        ns.append(w["hea_n"])
+        descs.append(hea(w["hea_n"], w["hea_layers"], w["seed"], k))
+    return ns, descs

@@ -185,14 +185,26 @@ sv_status sv_set_profiling(sv_handle h, int32_t on);
 typedef struct sv_batch *sv_batch_h;
 sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate *const *gates,
                           const int64_t *n_gates, const sv_options *opts, sv_batch_h *out);
-/* Launch the batch once (asynchronous).  use_graph != 0: the launch (counter reset + kernel) is
- * captured once into a CUDA graph and replayed on later runs. */
-sv_status sv_batch_run(sv_batch_h batch, int32_t use_graph);
+/* Launch the batch once (asynchronous).  flags: SV_BATCH_GRAPH -- the launch (counter reset +
+ * kernel) is captured once into a CUDA graph and replayed on later runs with the same flags;
+ * SV_BATCH_FROM_ZERO -- every state starts from |0..0> (Sec. IV.C initial state): the first
+ * section writes its chunks from the basis state instead of reading them, so the amplitudes
+ * need no prior sv_init_basis. */
+enum { SV_BATCH_GRAPH = 1, SV_BATCH_FROM_ZERO = 2 };
+sv_status sv_batch_run(sv_batch_h batch, int32_t flags);
 /* Wait for the last run; SV_ERR_TIMEOUT if a bounded wait in the launch expired. */
 sv_status sv_batch_sync(sv_batch_h batch);
-/* Number of chunk work items and sections in the batch. */
-sv_status sv_batch_info(sv_batch_h batch, int64_t *work_items, int32_t *sections);
+/* Number of chunk work items and of (state, section) sweeps in the batch, and the amplitude
+ * bytes one run reads and writes (2 x 8 B x 2^n per sweep of an n-qubit state).  NULL outputs
+ * are skipped. */
+sv_status sv_batch_info(sv_batch_h batch, int64_t *work_items, int32_t *sections, double *bytes_per_run);
 sv_status sv_batch_free(sv_batch_h batch);
+/* Autotune a batch: build it with chunk bits 10..13 (other fields from *base), time one run of
+ * each after a warm-up run, and write the fastest options to *best and its time to *best_ms.
+ * The circuits RUN on the given states: their amplitudes are overwritten (initialise them
+ * afterwards).  Same constraints as sv_batch_create. */
+sv_status sv_batch_tune(int32_t count, const sv_handle *states, const sv_gate *const *gates,
+                        const int64_t *n_gates, const sv_options *base, sv_options *best, double *best_ms);
 
 /* ------------------------------------------------------------------ autotuning */
 /* Time candidate executions of this circuit on a scratch n-qubit state of `dtype` (chunk bits

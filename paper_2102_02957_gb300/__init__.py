@@ -203,16 +203,19 @@ class Batch:
         o = options(**opts)
         check(lib().sv_batch_create(cnt, hs, gp, ng, ctypes.byref(o), ctypes.byref(self._h)))
 
-    def run(self, use_graph: bool = False):
-        check(lib().sv_batch_run(self._h, int(bool(use_graph))))
+    def run(self, use_graph: bool = False, from_zero: bool = False):
+        """One launch; from_zero: every state starts from |0..0> (no sv_init_basis needed)."""
+        flags = (_lib.SV_BATCH_GRAPH if use_graph else 0) | (_lib.SV_BATCH_FROM_ZERO if from_zero else 0)
+        check(lib().sv_batch_run(self._h, flags))
 
     def synchronize(self):
         check(lib().sv_batch_sync(self._h))
 
     def info(self):
-        items, sections = ctypes.c_int64(), ctypes.c_int32()
-        check(lib().sv_batch_info(self._h, ctypes.byref(items), ctypes.byref(sections)))
-        return items.value, sections.value
+        """(chunk work items, state sections, amplitude bytes read + written per run)."""
+        items, sections, nbytes = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+        check(lib().sv_batch_info(self._h, ctypes.byref(items), ctypes.byref(sections), ctypes.byref(nbytes)))
+        return items.value, sections.value, nbytes.value
 
     def close(self):
         if self._h:
@@ -226,6 +229,24 @@ class Batch:
             pass
 
 
+_OPT_KEYS = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned")
+
+
+def batch_tune(states, gate_lists, **base):
+    """sv_batch_tune: pick the batch's chunk bits by timing runs ON these states (their amplitudes
+    are overwritten).  Returns (options dict, milliseconds of one run)."""
+    gl = [np.ascontiguousarray(g) for g in gate_lists]
+    cnt = len(states)
+    hs = (ctypes.c_void_p * cnt)(*[s._h.value for s in states])
+    gp = (ctypes.c_void_p * cnt)(*[g.ctypes.data for g in gl])
+    ng = (ctypes.c_int64 * cnt)(*[len(g) for g in gl])
+    b = options(**base)
+    best = sv_options()
+    ms = ctypes.c_double()
+    check(lib().sv_batch_tune(cnt, hs, gp, ng, ctypes.byref(b), ctypes.byref(best), ctypes.byref(ms)))
+    return {k: getattr(best, k) for k in _OPT_KEYS}, ms.value
+
+
 def autotune(n: int, gates: np.ndarray, dtype="c64", **base):
     """sv_autotune: time candidate options for this circuit on a scratch state; returns
     (options dict, milliseconds of one application)."""
@@ -234,5 +255,4 @@ def autotune(n: int, gates: np.ndarray, dtype="c64", **base):
     ms = ctypes.c_double()
     check(lib().sv_autotune(n, DTYPES[dtype], gates.ctypes.data, len(gates), ctypes.byref(b), ctypes.byref(best),
                             ctypes.byref(ms)))
-    keys = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned")
-    return {k: getattr(best, k) for k in keys}, ms.value
+    return {k: getattr(best, k) for k in _OPT_KEYS}, ms.value

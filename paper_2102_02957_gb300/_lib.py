@@ -54,6 +54,8 @@ _lock = threading.Lock()
 _lib = None
 
 # name -> (restype, argtypes)
+SV_BATCH_GRAPH = 1
+SV_BATCH_FROM_ZERO = 2
 _VP = ctypes.c_void_p
 _SIGS = {
     "sv_gate_make": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _VP]),
@@ -80,7 +82,10 @@ _SIGS = {
     "sv_batch_create": (ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(sv_options), ctypes.POINTER(_VP)]),
     "sv_batch_run": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "sv_batch_sync": (ctypes.c_int, [_VP]),
-    "sv_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "sv_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "sv_batch_tune": (ctypes.c_int, [ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(sv_options),
+                                     ctypes.POINTER(sv_options), ctypes.POINTER(ctypes.c_double)]),
     "sv_batch_free": (ctypes.c_int, [_VP]),
     "sv_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(sv_options),
                                    ctypes.POINTER(sv_options), ctypes.POINTER(ctypes.c_double)]),

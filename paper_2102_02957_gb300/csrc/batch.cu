@@ -1,5 +1,6 @@
 // Batched execution (host side) and the autotuner.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "sv_internal.h"
@@ -14,12 +15,16 @@ struct sv_batch {
     size_t off_ops = 0, off_progs = 0, off_amps = 0, off_counters = 0, counters_bytes = 0;
     int nops = 0;
     int64_t total = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    double bytes = 0;
+    cudaGraph_t graph[2] = {nullptr, nullptr};     // per SV_BATCH_FROM_ZERO value
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<std::pair<void *, int>> idle;       // states without gates: (amplitudes, n)
     ~sv_batch() {
         if (work) cudaStreamSynchronize(work);
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
+        for (int k = 0; k < 2; ++k) {
+            if (exec[k]) cudaGraphExecDestroy(exec[k]);
+            if (graph[k]) cudaGraphDestroy(graph[k]);
+        }
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (work) cudaStreamDestroy(work);
@@ -30,7 +35,9 @@ struct sv_batch {
 namespace sv {
 namespace {
 
-void launch_once(sv_batch *b) {
+void launch_once(sv_batch *b, int from_zero) {
+    if (from_zero)
+        for (const auto &z : b->idle) launch_init_basis(SV_C64, z.first, z.second, 0, b->work);
     unsigned char *c = b->dev + b->off_counters;
     check_cuda(cudaMemsetAsync(c, 0, b->counters_bytes, b->work), "cudaMemsetAsync(batch counters)");
     int *ops_done = reinterpret_cast<int *>(c);
@@ -38,8 +45,8 @@ void launch_once(sv_batch *b) {
     unsigned long long *next = reinterpret_cast<unsigned long long *>(c + (((size_t)(b->count + b->nops) * 4 + 15) & ~size_t(15)));
     int *err = reinterpret_cast<int *>(next + 1);
     launch_batch(b->dev + b->off_ops, b->nops, b->dev + b->off_progs,
-                 reinterpret_cast<void *const *>(b->dev + b->off_amps), ops_done, chunks_done, next, b->total, err,
-                 b->work);
+                 reinterpret_cast<void *const *>(b->dev + b->off_amps), ops_done, chunks_done, next, b->total,
+                 from_zero, err, b->work);
 }
 
 int *batch_err(sv_batch *b) {
@@ -102,11 +109,17 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
         o.chunk_bits = std::min(std::max(o.chunk_bits, 6), kBatchMaxChunkBits);
         o.gather_pinned = std::min(4, std::min(o.chunk_bits, h->n) - 2);
         o.reserve = 0;
+        o.restore_layout = 1;
+        for (int64_t i = 0; i < n_gates[s]; ++i)
+            if (gates[s][i].flags & SV_GATE_SWAP)
+                fail(SV_ERR_UNSUPPORTED, "sv_batch_create: SWAP relabels are not batched");
         o.seg_bits = 4;
         o.use_tc = 0;
         std::unique_ptr<sv_plan> plan(plan_blocking(h->n, gates[s], n_gates[s], o));
+        if (plan->ops.empty()) b->idle.emplace_back(h->amp, h->n);
         int opno = 0;
         for (const PlanOp &op : plan->ops) {
+            if (op.gates.empty()) continue;
             if (op.kind == 1 || op.kind == 3) fail(SV_ERR_UNSUPPORTED, "sv_batch_create: SWAP relabels are not batched");
             // chunk-local order: contiguous low run, then the other chunk bits ascending
             const int n = h->n;
@@ -127,6 +140,8 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                 }
             }
             bo.ce = k;
+            if (low < 4 || k - low > kBatchMaxChunkBits - 4)
+                fail(SV_ERR_PLAN, "sv_batch_create: batched chunk without a 4-bit contiguous low run");
             bo.nchunks = int64_t(1) << (n - k);
             std::vector<BlockGate> loc = op.gates;
             for (BlockGate &g : loc)
@@ -142,13 +157,21 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                     segs.push_back(std::move(part));
                 }
             }
-            // programs of at most kBatchMaxProgBytes: long sections become consecutive sweeps
+            // the section's program in pieces of at most kBatchMaxProgBytes, each a 16-byte header
+            // {nseg, ngate, bytes, 0} + register groups + gate records; the kernel runs the
+            // pieces one after another on the resident chunk
+            align(256);
+            BatchOp sec = bo;
+            sec.op = opno++;
+            sec.prog_off = (uint32_t)progs.size();
+            sec.npiece = 0;
             size_t p0 = 0;
             while (p0 < segs.size()) {
                 size_t p1 = p0, gates_in = 0;
                 while (p1 < segs.size()) {
                     const size_t g_next = gates_in + segs[p1].gates.size();
-                    const size_t bytes = ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + g_next * sizeof(DevGate<float>);
+                    const size_t bytes =
+                        16 + ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + g_next * sizeof(DevGate<float>);
                     if (bytes > (size_t)kBatchMaxProgBytes && p1 > p0) break;
                     if (bytes > (size_t)kBatchMaxProgBytes) fail(SV_ERR_UNSUPPORTED, "register group too large");
                     gates_in = g_next;
@@ -157,35 +180,42 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                 std::vector<DevSeg> ds;
                 std::vector<DevGate<float>> dg;
                 for (size_t q = p0; q < p1; ++q) {
+                    const HostSeg &hs = segs[q];
                     DevSeg d;
                     std::memset(&d, 0, sizeof(d));
-                    d.r = (int8_t)segs[q].r;
-                    for (int t = 0; t < segs[q].r; ++t) d.pos[t] = (int8_t)segs[q].pos[t];
+                    d.r = (int8_t)hs.r;
+                    for (int t = 0; t < hs.r; ++t) d.pos[t] = (int8_t)hs.pos[t];
+                    for (int t = 0; t < 5; ++t) d.lane[t] = (int8_t)hs.lane[t];
+                    d.nrest = (int8_t)hs.nrest;
+                    for (int t = 0; t < hs.nrest; ++t) d.rest[t] = (int8_t)hs.rest[t];
+                    // the chunk arrives and leaves in the natural layout
+                    d.flags = (int8_t)((q == 0 ? 1 : 0) | (q + 1 == segs.size() ? 2 : 0));
                     d.g0 = (int16_t)dg.size();
-                    for (int32_t gi : segs[q].gates) {
+                    for (int32_t gi : hs.gates) {
                         DevGate<float> g;
-                        encode_gate<float>(gates[s][loc[gi].gi], loc[gi], segs[q], g);
+                        encode_gate<float>(gates[s][loc[gi].gi], loc[gi], hs, g);
                         dg.push_back(g);
                     }
                     d.g1 = (int16_t)dg.size();
                     ds.push_back(d);
                 }
-                align(256);
-                BatchOp piece = bo;
-                piece.op = opno++;
-                piece.prog_off = (uint32_t)progs.size();
-                piece.nseg = (int)ds.size();
-                piece.ngate = (int)dg.size();
+                const size_t at = progs.size();
+                progs.resize(at + 16, 0);
                 const unsigned char *p = reinterpret_cast<const unsigned char *>(ds.data());
                 progs.insert(progs.end(), p, p + ds.size() * sizeof(DevSeg));
                 align(16);
                 p = reinterpret_cast<const unsigned char *>(dg.data());
                 progs.insert(progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
                 align(16);
-                piece.prog_bytes = (uint32_t)(progs.size() - piece.prog_off);
-                per_state[(size_t)s].push_back(piece);
+                const int32_t hd[4] = {(int32_t)ds.size(), (int32_t)dg.size(), (int32_t)(progs.size() - at), 0};
+                std::memcpy(progs.data() + at, hd, sizeof(hd));
+                ++sec.npiece;
                 p0 = p1;
             }
+            sec.prog_bytes = (uint32_t)(progs.size() - sec.prog_off);
+            if (sec.npiece == 0) continue;
+            b->bytes += 2.0 * 8.0 * std::ldexp(1.0, n);
+            per_state[(size_t)s].push_back(sec);
         }
     }
     // queue order: section level by section level, round-robin over the states
@@ -235,29 +265,31 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
     SV_API_END
 }
 
-sv_status sv_batch_run(sv_batch_h b, int32_t use_graph) {
+sv_status sv_batch_run(sv_batch_h b, int32_t flags) {
     SV_API_BEGIN
     if (!b) fail(SV_ERR_ARG, "null batch");
+    if (flags & ~(SV_BATCH_GRAPH | SV_BATCH_FROM_ZERO)) fail(SV_ERR_ARG, "sv_batch_run: unknown flag");
+    const int use_graph = flags & SV_BATCH_GRAPH, fz = (flags & SV_BATCH_FROM_ZERO) ? 1 : 0;
     // the batch's stream follows the states' stream, and the states' stream follows the batch
     check_cuda(cudaEventRecord(b->ev_in, b->stream), "cudaEventRecord");
     check_cuda(cudaStreamWaitEvent(b->work, b->ev_in, 0), "cudaStreamWaitEvent");
     if (!use_graph) {
-        launch_once(b);
+        launch_once(b, fz);
     } else {
-        if (!b->exec) {
+        if (!b->exec[fz]) {
             check_cuda(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
             try {
-                launch_once(b);
+                launch_once(b, fz);
             } catch (...) {
                 cudaGraph_t g = nullptr;
                 cudaStreamEndCapture(b->work, &g);
                 if (g) cudaGraphDestroy(g);
                 throw;
             }
-            check_cuda(cudaStreamEndCapture(b->work, &b->graph), "cudaStreamEndCapture");
-            check_cuda(cudaGraphInstantiate(&b->exec, b->graph, 0), "cudaGraphInstantiate");
+            check_cuda(cudaStreamEndCapture(b->work, &b->graph[fz]), "cudaStreamEndCapture");
+            check_cuda(cudaGraphInstantiate(&b->exec[fz], b->graph[fz], 0), "cudaGraphInstantiate");
         }
-        check_cuda(cudaGraphLaunch(b->exec, b->work), "cudaGraphLaunch");
+        check_cuda(cudaGraphLaunch(b->exec[fz], b->work), "cudaGraphLaunch");
     }
     check_cuda(cudaEventRecord(b->ev_out, b->work), "cudaEventRecord");
     check_cuda(cudaStreamWaitEvent(b->stream, b->ev_out, 0), "cudaStreamWaitEvent");
@@ -275,11 +307,53 @@ sv_status sv_batch_sync(sv_batch_h b) {
     SV_API_END
 }
 
-sv_status sv_batch_info(sv_batch_h b, int64_t *items, int32_t *sections) {
+sv_status sv_batch_info(sv_batch_h b, int64_t *items, int32_t *sections, double *bytes_per_run) {
     SV_API_BEGIN
     if (!b) fail(SV_ERR_ARG, "null batch");
     if (items) *items = b->total;
     if (sections) *sections = b->nops;
+    if (bytes_per_run) *bytes_per_run = b->bytes;
+    SV_API_END
+}
+
+sv_status sv_batch_tune(int32_t count, const sv_handle *states, const sv_gate *const *gates, const int64_t *n_gates,
+                        const sv_options *base, sv_options *best, double *best_ms) {
+    SV_API_BEGIN
+    if (!best || !states || count <= 0) fail(SV_ERR_ARG, "sv_batch_tune: bad arguments");
+    sv_options b0;
+    if (base) b0 = *base; else sv_options_default(&b0);
+    cudaStream_t st = states[0]->stream;
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    double best_t = 1e300;
+    sv_options best_o = b0;
+    sv_status last = SV_OK;
+    for (int c = 10; c <= kBatchMaxChunkBits; ++c) {
+        sv_options o = b0;
+        o.chunk_bits = c;
+        sv_batch_h bt = nullptr;
+        last = sv_batch_create(count, states, gates, n_gates, &o, &bt);
+        if (last != SV_OK) continue;
+        float ms = -1.f;
+        if ((last = sv_batch_run(bt, SV_BATCH_FROM_ZERO)) == SV_OK && (last = sv_batch_sync(bt)) == SV_OK) {
+            cudaEventRecord(e0, st);
+            last = sv_batch_run(bt, SV_BATCH_FROM_ZERO);
+            cudaEventRecord(e1, st);
+            if (last == SV_OK && (last = sv_batch_sync(bt)) == SV_OK && cudaEventSynchronize(e1) == cudaSuccess)
+                cudaEventElapsedTime(&ms, e0, e1);
+        }
+        sv_batch_free(bt);
+        if (ms >= 0.f && ms < best_t) {
+            best_t = ms;
+            best_o = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_t >= 1e300) return last != SV_OK ? last : SV_ERR_UNSUPPORTED;
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
     SV_API_END
 }
 

@@ -1,0 +1,323 @@
+// Register-group engine shared by the blocking-section kernels: gates applied to 2^R amplitudes
+// held in registers, with the amplitudes read from / written to a chunk in shared memory
+// (swizzled layout, host-chosen lane layouts; see sv_internal.h for the swizzle table).
+#pragma once
+#include <stdint.h>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+// Swizzle patterns V[k] (see sv_internal.h); the host picks lane layouts from the same table.
+__constant__ int c_swz64[24] = {SV_SWZ64_LIST};
+__constant__ int c_swz128[24] = {SV_SWZ128_LIST};
+
+__device__ __forceinline__ int insert0(int x, int p) { return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1)); }
+
+template <typename T>
+__device__ __forceinline__ void cmul_acc(T &yr, T &yi, T mr, T mi, T xr, T xi) {
+    yr = fma(mr, xr, yr);
+    yr = fma(-mi, xi, yr);
+    yi = fma(mr, xi, yi);
+    yi = fma(mi, xr, yi);
+}
+
+// ---- explicit shared-memory access with 32-bit shared addresses.  Chunk data goes through
+// volatile accesses (ordered with the barriers); the section program is read-only after the
+// kernel's first barrier, so its loads are pure and the compiler may reuse them across groups.
+template <typename T> struct SM;
+template <> struct SM<float> {
+    static __device__ __forceinline__ void ld(uint32_t a, float &x, float &y) {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+    }
+    static __device__ __forceinline__ void st(uint32_t a, float x, float y) {
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+    }
+    static __device__ __forceinline__ void ldc4(uint32_t a, float &x, float &y, float &z, float &w) {
+        asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+    }
+};
+template <> struct SM<double> {
+    static __device__ __forceinline__ void ld(uint32_t a, double &x, double &y) {
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+    }
+    static __device__ __forceinline__ void st(uint32_t a, double x, double y) {
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(x), "d"(y) : "memory");
+    }
+    static __device__ __forceinline__ void ldc4(uint32_t a, double &x, double &y, double &z, double &w) {
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(z), "=d"(w) : "r"(a + 16));
+    }
+};
+
+__device__ __forceinline__ int lds_s8(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int lds_s16(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void ldc_i4(uint32_t a, int &x, int &y, int &z, int &w) {
+    asm("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void load_mat(uint32_t a, T (&m)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; k += 4) SM<T>::ldc4(a + k * (uint32_t)sizeof(T), m[k], m[k + 1], m[k + 2], m[k + 3]);
+}
+
+template <typename T, int NA, int A>
+__device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T m[8];
+    load_mat<T, 8>(ma, m);
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        if (x & (1 << A)) continue;
+        const int y = x | (1 << A);
+        const T ar = r[x], ai = i[x], br = r[y], bi = i[y];
+        T pr = 0, pi = 0, qr = 0, qi = 0;
+        cmul_acc(pr, pi, m[0], m[1], ar, ai);
+        cmul_acc(pr, pi, m[2], m[3], br, bi);
+        cmul_acc(qr, qi, m[4], m[5], ar, ai);
+        cmul_acc(qr, qi, m[6], m[7], br, bi);
+        r[x] = pr; i[x] = pi; r[y] = qr; i[y] = qi;
+    }
+}
+
+template <typename T, int NA, int A>
+__device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T d[4];
+    load_mat<T, 4>(ma, d);
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        const T dr = (x & (1 << A)) ? d[2] : d[0], di = (x & (1 << A)) ? d[3] : d[1];
+        const T xr = r[x], xi = i[x];
+        r[x] = fma(dr, xr, -di * xi);
+        i[x] = fma(dr, xi, di * xr);
+    }
+}
+
+template <typename T, int NA, int A, int B>
+__device__ __forceinline__ void ap_dense2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T mm[32];
+    load_mat<T, 32>(ma, mm);
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        if (x & ((1 << A) | (1 << B))) continue;
+        const int id[4] = {x, x | (1 << A), x | (1 << B), x | (1 << A) | (1 << B)};
+        T xr[4], xi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { xr[k] = r[id[k]]; xi[k] = i[id[k]]; }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            T yr = 0, yi = 0;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) cmul_acc(yr, yi, mm[2 * (4 * rr + cc)], mm[2 * (4 * rr + cc) + 1], xr[cc], xi[cc]);
+            r[id[rr]] = yr;
+            i[id[rr]] = yi;
+        }
+    }
+}
+
+template <typename T, int NA, int A, int B>
+__device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T d[8];
+    load_mat<T, 8>(ma, d);
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        const int l = ((x >> A) & 1) | (((x >> B) & 1) << 1);
+        const T dr = d[2 * l], di = d[2 * l + 1];
+        const T xr = r[x], xi = i[x];
+        r[x] = fma(dr, xr, -di * xi);
+        i[x] = fma(dr, xi, di * xr);
+    }
+}
+
+template <typename T, int NA, int A, int B>
+__device__ __forceinline__ void ap_perm2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
+    T pm[4];
+    load_mat<T, 4>(ma, pm);
+    const int p0 = (int)pm[0], p1 = (int)pm[1], p2 = (int)pm[2], p3 = (int)pm[3];
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        if (x & ((1 << A) | (1 << B))) continue;
+        const int id[4] = {x, x | (1 << A), x | (1 << B), x | (1 << A) | (1 << B)};
+        T xr[4], xi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { xr[k] = r[id[k]]; xi[k] = i[id[k]]; }
+        const int p[4] = {p0, p1, p2, p3};
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int s = p[rr];
+            r[id[rr]] = s == 0 ? xr[0] : s == 1 ? xr[1] : s == 2 ? xr[2] : xr[3];
+            i[id[rr]] = s == 0 ? xi[0] : s == 1 ? xi[1] : s == 2 ? xi[2] : xi[3];
+        }
+    }
+}
+
+// Bit flip on register bit A: a pure exchange of registers (no arithmetic).
+template <typename T, int NA, int A>
+__device__ __forceinline__ void ap_x1(T (&r)[NA], T (&i)[NA]) {
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        if (x & (1 << A)) continue;
+        const int y = x | (1 << A);
+        T t = r[x]; r[x] = r[y]; r[y] = t;
+        t = i[x]; i[x] = i[y]; i[y] = t;
+    }
+}
+
+// Exchange of the local two-qubit basis states U and V (index = bit A + 2 * bit B) in every
+// 4-amplitude block: CNOT and SWAP, again without arithmetic.
+template <typename T, int NA, int A, int B, int U, int V>
+__device__ __forceinline__ void ap_xchg2(T (&r)[NA], T (&i)[NA]) {
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+        if (x & ((1 << A) | (1 << B))) continue;
+        const int id[4] = {x, x | (1 << A), x | (1 << B), x | (1 << A) | (1 << B)};
+        T t = r[id[U]]; r[id[U]] = r[id[V]]; r[id[V]] = t;
+        t = i[id[U]]; i[id[U]] = i[id[V]]; i[id[V]] = t;
+    }
+}
+
+// Dispatch a gate on the register bits (a, b) -- compile-time bit positions via templates.
+template <typename T, int R, int A>
+__device__ __forceinline__ void one(int op, T (&r)[1 << R], T (&i)[1 << R], uint32_t m) {
+    if (op == OP_DENSE1) ap_dense1<T, 1 << R, A>(r, i, m);
+    else if (op == OP_X1) ap_x1<T, 1 << R, A>(r, i);
+    else ap_diag1<T, 1 << R, A>(r, i, m);
+}
+
+template <typename T, int R, int A, int B>
+__device__ __forceinline__ void two(int op, T (&r)[1 << R], T (&i)[1 << R], uint32_t m) {
+    if (op == OP_DENSE2) ap_dense2<T, 1 << R, A, B>(r, i, m);
+    else if (op == OP_DIAG2) ap_diag2<T, 1 << R, A, B>(r, i, m);
+    else if (op == OP_CXA) ap_xchg2<T, 1 << R, A, B, 1, 3>(r, i);
+    else if (op == OP_CXB) ap_xchg2<T, 1 << R, A, B, 2, 3>(r, i);
+    else if (op == OP_SWAP2) ap_xchg2<T, 1 << R, A, B, 1, 2>(r, i);
+    else ap_perm2<T, 1 << R, A, B>(r, i, m);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void apply_gate(int op, int code, uint32_t m, T (&r)[1 << R], T (&i)[1 << R]) {
+    if (op == OP_DENSE1 || op == OP_DIAG1 || op == OP_X1) {
+        switch (code) {
+            case 0: one<T, R, 0>(op, r, i, m); break;
+            case 1: one<T, R, 1>(op, r, i, m); break;
+            case 2: one<T, R, 2>(op, r, i, m); break;
+            case 3: one<T, R, 3>(op, r, i, m); break;
+            case 4: if constexpr (R > 4) one<T, R, 4>(op, r, i, m); break;
+            default: break;
+        }
+    } else {
+        switch (code) {
+            case 0 * 8 + 1: two<T, R, 0, 1>(op, r, i, m); break;
+            case 0 * 8 + 2: two<T, R, 0, 2>(op, r, i, m); break;
+            case 0 * 8 + 3: two<T, R, 0, 3>(op, r, i, m); break;
+            case 1 * 8 + 2: two<T, R, 1, 2>(op, r, i, m); break;
+            case 1 * 8 + 3: two<T, R, 1, 3>(op, r, i, m); break;
+            case 2 * 8 + 3: two<T, R, 2, 3>(op, r, i, m); break;
+            case 0 * 8 + 4: if constexpr (R > 4) two<T, R, 0, 4>(op, r, i, m); break;
+            case 1 * 8 + 4: if constexpr (R > 4) two<T, R, 1, 4>(op, r, i, m); break;
+            case 2 * 8 + 4: if constexpr (R > 4) two<T, R, 2, 4>(op, r, i, m); break;
+            case 3 * 8 + 4: if constexpr (R > 4) two<T, R, 3, 4>(op, r, i, m); break;
+            default: break;
+        }
+    }
+}
+
+constexpr int kMaxRest = 8;  // chunk bits above the lanes per register group (c <= R + 5 + 8)
+
+// One register group over the chunk in shared memory.  `buf`, `seg` and `gates` are shared
+// addresses of the chunk buffer, the group descriptor and the section's gate records.  Each
+// thread handles KU groups at a time so that every gate matrix is read once for all of them.
+template <typename T, int R, int NC, int KU>
+__device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t gates, int ctid, const int *swz,
+                                            int c) {
+    constexpr int NA = 1 << R;
+    constexpr int SH = sizeof(T) == 4 ? 3 : 4;  // log2 bytes per amplitude
+    // descriptor (DevSeg layout: pos[8] lane[5] nrest flags r rest[16] g0 g1)
+    int po[R], pf[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int p = lds_s8(seg + j);
+        po[j] = 1 << p;
+        pf[j] = po[j] ^ swz[p];
+    }
+    const int lane = ctid & 31;
+    int lbase = 0, lfb = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int p = lds_s8(seg + 8 + j);
+        if ((lane >> j) & 1) { lbase |= 1 << p; lfb ^= swz[p]; }
+    }
+    const int nrest = lds_s8(seg + 13), flags = lds_s8(seg + 14);
+    int rpo[kMaxRest], rpf[kMaxRest];
+#pragma unroll
+    for (int j = 0; j < kMaxRest; ++j) {
+        const int p = j < nrest ? lds_s8(seg + 16 + j) : 0;
+        rpo[j] = j < nrest ? 1 << p : 0;
+        rpf[j] = j < nrest ? swz[p] : 0;
+    }
+    const int g0 = lds_s16(seg + 32), g1 = lds_s16(seg + 34);
+    const int G = 1 << (c - R);
+
+    for (int gb = ctid; gb < G; gb += NC * KU) {
+        T re[KU][NA], im[KU][NA];
+        int base[KU], sbase[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int hi = (gb + u * NC) >> 5;
+            int bs = lbase, fb = lfb;
+#pragma unroll
+            for (int j = 0; j < kMaxRest; ++j)
+                if ((hi >> j) & 1) { bs |= rpo[j]; fb ^= rpf[j]; }
+            base[u] = bs;
+            sbase[u] = bs ^ fb;
+            if (gb + u * NC < G) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    int o = 0, f = 0;
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
+                    const int a = (flags & 1) ? (base[u] | o) : (sbase[u] ^ f);
+                    SM<T>::ld(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                }
+            }
+        }
+        for (int gi = g0; gi < g1; ++gi) {
+            const uint32_t ga = gates + (uint32_t)gi * (uint32_t)sizeof(DevGate<T>);
+            int op, ra, rb, code;
+            ldc_i4(ga, op, ra, rb, code);
+#pragma unroll
+            for (int u = 0; u < KU; ++u) apply_gate<T, R>(op, code, ga + 16, re[u], im[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            if (gb + u * NC < G) {
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    int o = 0, f = 0;
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
+                    const int a = (flags & 2) ? (base[u] | o) : (sbase[u] ^ f);
+                    SM<T>::st(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace sv

@@ -3,13 +3,15 @@
 //
 // Each state is planned with gathered chunks (Sec. IV.A transpiler without data movement);
 // a state whose qubits fit one chunk has a single section and runs its whole circuit in one
-// shared-memory residency.  The launch drains a global work queue of (state, section, chunk)
+// shared-memory residency (a long program is streamed through shared memory in pieces).  The launch drains a global work queue of (state, section, chunk)
 // items.  Items are ordered section level by section level, round-robin over the states, so a
 // state's section o+1 is queued after all of its section o.  A CTA that takes a chunk of
 // section o waits (bounded) until every chunk of the state's earlier sections is done; since
 // every earlier item was taken by a CTA that is running and never waits on a later item, the
 // queue always drains.  Completion counters use release/acquire ordering and chunk data goes
-// through L2 (ld.global.cg / st.global.cg) so that no stale L1 line is read.
+// through L2 (cp.async.cg / st.global.cg) so that no stale L1 line is read.  Inside a chunk the
+// section's register groups run on the same engine as the single-state blocking kernel.
+#include "block_core.cuh"
 #include "ptx.cuh"
 #include "sv_internal.h"
 
@@ -26,93 +28,6 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-__device__ __forceinline__ void cmul_acc(float &yr, float &yi, float mr, float mi, float xr, float xi) {
-    yr = fmaf(mr, xr, yr);
-    yr = fmaf(-mi, xi, yr);
-    yi = fmaf(mr, xi, yi);
-    yi = fmaf(mi, xr, yi);
-}
-
-// Dense / diagonal / permutation gates on a register group of 16 amplitudes (runtime bits).
-template <int A>
-__device__ __forceinline__ void g1(float (&r)[16], float (&i)[16], const DevGate<float> &g) {
-    const float *m = g.m;
-#pragma unroll
-    for (int x = 0; x < 16; ++x) {
-        if (x & (1 << A)) continue;
-        const int y = x | (1 << A);
-        const float ar = r[x], ai = i[x], br = r[y], bi = i[y];
-        float pr = 0, pi = 0, qr = 0, qi = 0;
-        if (g.op == OP_DENSE1) {
-            cmul_acc(pr, pi, m[0], m[1], ar, ai);
-            cmul_acc(pr, pi, m[2], m[3], br, bi);
-            cmul_acc(qr, qi, m[4], m[5], ar, ai);
-            cmul_acc(qr, qi, m[6], m[7], br, bi);
-        } else {
-            cmul_acc(pr, pi, m[0], m[1], ar, ai);
-            cmul_acc(qr, qi, m[2], m[3], br, bi);
-        }
-        r[x] = pr; i[x] = pi; r[y] = qr; i[y] = qi;
-    }
-}
-
-template <int A, int B>
-__device__ __forceinline__ void g2(float (&r)[16], float (&i)[16], const DevGate<float> &g) {
-    float mm[32];
-    if (g.op == OP_DENSE2) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) mm[k] = g.m[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) mm[k] = 0.f;
-        if (g.op == OP_DIAG2) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { mm[2 * (5 * q)] = g.m[2 * q]; mm[2 * (5 * q) + 1] = g.m[2 * q + 1]; }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) mm[2 * (4 * q + cc)] = ((int)g.m[q] == cc) ? 1.f : 0.f;
-        }
-    }
-#pragma unroll
-    for (int x = 0; x < 16; ++x) {
-        if (x & ((1 << A) | (1 << B))) continue;
-        const int id[4] = {x, x | (1 << A), x | (1 << B), x | (1 << A) | (1 << B)};
-        float xr[4], xi[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { xr[k] = r[id[k]]; xi[k] = i[id[k]]; }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float yr = 0, yi = 0;
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) cmul_acc(yr, yi, mm[2 * (4 * q + cc)], mm[2 * (4 * q + cc) + 1], xr[cc], xi[cc]);
-            r[id[q]] = yr;
-            i[id[q]] = yi;
-        }
-    }
-}
-
-__device__ __forceinline__ void apply(float (&r)[16], float (&i)[16], const DevGate<float> &g) {
-    if (g.op == OP_DENSE1 || g.op == OP_DIAG1) {
-        switch (g.code) {
-            case 0: g1<0>(r, i, g); break;
-            case 1: g1<1>(r, i, g); break;
-            case 2: g1<2>(r, i, g); break;
-            default: g1<3>(r, i, g); break;
-        }
-    } else {
-        switch (g.code) {
-            case 0 * 8 + 1: g2<0, 1>(r, i, g); break;
-            case 0 * 8 + 2: g2<0, 2>(r, i, g); break;
-            case 0 * 8 + 3: g2<0, 3>(r, i, g); break;
-            case 1 * 8 + 2: g2<1, 2>(r, i, g); break;
-            case 1 * 8 + 3: g2<1, 3>(r, i, g); break;
-            default: g2<2, 3>(r, i, g); break;
-        }
-    }
-}
-
 __device__ __forceinline__ int64_t deposit(int64_t v, const int8_t *bits, int nbits) {
     int64_t x = 0;
     for (int k = 0; k < nbits; ++k)
@@ -120,107 +35,131 @@ __device__ __forceinline__ int64_t deposit(int64_t v, const int8_t *bits, int nb
     return x;
 }
 
-// Shared-memory slot of chunk-local amplitude i: the low four bits are XORed with the higher
-// nibbles, so that 16 consecutive threads whose indices differ outside a register group hit
-// distinct banks whichever four bits the group holds.
-__device__ __forceinline__ int slot(int i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15); }
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Last op whose first item is <= item, searching forward from `k` (a CTA's items increase).
+__device__ __forceinline__ int find_op(const BatchOp *ops, int nops, int64_t item, int k) {
+    if (ops[k].first > item) k = 0;
+    int step = 1, hi = k;
+    while (hi + step < nops && ops[hi + step].first <= item) {
+        hi += step;
+        step <<= 1;
+    }
+    int lo = hi, top = min(nops - 1, hi + step - 1);
+    while (lo < top) {
+        const int mid = (lo + top + 1) / 2;
+        if (ops[mid].first <= item) lo = mid; else top = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kMaxRuns = 1 << (kBatchMaxChunkBits - 4);  // chunk runs above a low run of >= 4 bits
+
+__device__ __forceinline__ void copy_prog(unsigned char *dst, const unsigned char *src, int bytes) {
+    for (int k = threadIdx.x * 16; k < bytes; k += NCB * 16)
+        *reinterpret_cast<uint4 *>(dst + k) = *reinterpret_cast<const uint4 *>(src + k);
+}  // chunk runs above a low run of >= 4 bits
 
 __global__ void __launch_bounds__(NCB) k_batch(const BatchOp *__restrict__ ops, int nops,
                                                const unsigned char *__restrict__ progs, float2 *const *amps,
                                                int *ops_done, int *chunks_done, unsigned long long *next,
-                                               int64_t total, int *err) {
+                                               int64_t total, int from_zero, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *chunk = reinterpret_cast<float2 *>(smem);
+    const uint32_t chunk_s = ptx::smem_addr(chunk);
     unsigned char *sprog = smem + (size_t(1) << kBatchMaxChunkBits) * sizeof(float2);
-    __shared__ int64_t s_item;
+    __shared__ int64_t s_item, s_next;
     __shared__ int s_op, s_cached, s_abort;
     __shared__ BatchOp s_bop;
-    if (threadIdx.x == 0) { s_cached = -1; s_abort = 0; }
+    __shared__ int64_t s_dep[kMaxRuns];  // state-index bits of each run of the chunk
+    if (threadIdx.x == 0) {
+        s_cached = -1;
+        s_abort = 0;
+        s_op = 0;
+        s_next = (int64_t)atomicAdd(next, 1ull);
+    }
     __syncthreads();
     while (true) {
         if (threadIdx.x == 0) {
-            s_item = (int64_t)atomicAdd(next, 1ull);
-            int k = -1;
-            if (s_item < total) {  // last op with first <= item
-                int lo = 0, hi = nops - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) / 2;
-                    if (ops[mid].first <= s_item) lo = mid; else hi = mid - 1;
-                }
-                k = lo;
+            const int64_t item = s_next;
+            s_item = item;
+            if (item < total) {
+                const int k = find_op(ops, nops, item, s_op);
+                if (k != s_op || s_cached < 0) s_bop = ops[k];
+                s_op = k;
+                // take the next index now; its lookup and wait happen after this item
+                s_next = (int64_t)atomicAdd(next, 1ull);
                 // earlier sections of this state must be complete
-                const BatchOp &op = ops[k];
-                const uint64_t t0 = ptx::globaltimer();
-                while (ld_acquire(&ops_done[op.state]) < op.op) {
-                    if (ptx::globaltimer() - t0 > kWaitLimitNs || *(volatile int *)err) {
-                        atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
-                        s_abort = 1;
-                        break;
+                const int st = s_bop.state, need = s_bop.op;
+                if (ld_acquire(&ops_done[st]) < need) {
+                    const uint64_t t0 = ptx::globaltimer();
+                    while (ld_acquire(&ops_done[st]) < need) {
+                        if (ptx::globaltimer() - t0 > kWaitLimitNs || *(volatile int *)err) {
+                            atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+                            s_abort = 1;
+                            break;
+                        }
+                        __nanosleep(200);
                     }
-                    __nanosleep(256);
                 }
             }
-            s_op = k;
-            if (k >= 0) s_bop = ops[k];
         }
         __syncthreads();
         if (s_item >= total || s_abort) break;
         const BatchOp &op = s_bop;
         const int64_t j = s_item - op.first;
-        const int ce = op.ce;
-        // section program (register groups + gates) into shared memory, once per section
-        if (s_cached != s_op) {
-            const int bytes = op.prog_bytes;
-            for (int k = threadIdx.x * 16; k < bytes; k += NCB * 16)
-                *reinterpret_cast<uint4 *>(sprog + k) = *reinterpret_cast<const uint4 *>(progs + op.prog_off + k);
+        const int ce = op.ce, low = op.low;
+        const bool fresh = s_cached != s_op;
+        // run table once per section; a one-piece program stays in shared memory across chunks
+        if (fresh) {
+            for (int r = threadIdx.x; r < (1 << (ce - low)); r += NCB) s_dep[r] = deposit(r, op.high, op.nhigh);
+            if (op.npiece == 1) copy_prog(sprog, progs + op.prog_off, op.prog_bytes);
+            __syncthreads();
         }
-        // gather chunk j: local index = (high bits | low run); state index = outer(j) | high | low
         float2 *amp = amps[op.state];
         const int64_t obase = deposit(j, op.outer, op.nouter);
-        const int low = op.low;
-        for (int e = threadIdx.x; e < (1 << ce); e += NCB) {
-            const int r = e >> low, l = e & ((1 << low) - 1);
-            const int64_t gidx = obase | deposit(r, op.high, op.nhigh) | l;
-            chunk[slot(e)] = __ldcg(amp + gidx);
+        const int lmask = (1 << low) - 1, npairs = 1 << (ce - 1);
+        if (from_zero && op.op == 0) {
+            // first section of a state started from |0..0>: the chunk holding index 0 is e_0
+            for (int f = threadIdx.x; f < npairs; f += NCB)
+                *reinterpret_cast<float4 *>(chunk + 2 * f) = make_float4((j == 0 && f == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        } else {
+#pragma unroll 4
+            for (int f = threadIdx.x; f < npairs; f += NCB) {
+                const int e = 2 * f;
+                const int64_t gidx = obase | s_dep[e >> low] | (e & lmask);
+                cp_async16(chunk_s + 8u * (uint32_t)e, amp + gidx);
+            }
+            cp_async_wait_all();
         }
         __syncthreads();
         if (threadIdx.x == 0) s_cached = s_op;
-        const DevSeg *segs = reinterpret_cast<const DevSeg *>(sprog);
-        const DevGate<float> *gates =
-            reinterpret_cast<const DevGate<float> *>(sprog + ((op.nseg * sizeof(DevSeg) + 15) & ~size_t(15)));
-        for (int si = 0; si < op.nseg; ++si) {
-            const DevSeg &sg = segs[si];
-            const int G = 1 << (ce - RB);
-            for (int g = threadIdx.x; g < G; g += NCB) {
-                // natural layout throughout: group base = bits of g inserted around the group bits
-                int base = g;
-#pragma unroll
-                for (int q = 0; q < RB; ++q) {
-                    const int p = sg.pos[q];
-                    base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1));
-                }
-                int off[16];
-#pragma unroll
-                for (int b = 0; b < 16; ++b) {
-                    int o = 0;
-#pragma unroll
-                    for (int q = 0; q < RB; ++q)
-                        if (b & (1 << q)) o |= 1 << sg.pos[q];
-                    off[b] = base | o;
-                }
-                float re[16], im[16];
-#pragma unroll
-                for (int b = 0; b < 16; ++b) { const float2 v = chunk[slot(off[b])]; re[b] = v.x; im[b] = v.y; }
-                for (int gi = sg.g0; gi < sg.g1; ++gi) apply(re, im, gates[gi]);
-#pragma unroll
-                for (int b = 0; b < 16; ++b) chunk[slot(off[b])] = make_float2(re[b], im[b]);
+        // register groups, piece by piece: the first group reads the natural layout, the last
+        // writes it back natural
+        uint32_t poff = op.prog_off;
+        for (int pc = 0; pc < op.npiece; ++pc) {
+            const int4 hd = *reinterpret_cast<const int4 *>(progs + poff);
+            if (op.npiece > 1) {
+                copy_prog(sprog, progs + poff, hd.z);
+                __syncthreads();
             }
-            __syncthreads();
+            const uint32_t seg_s = ptx::smem_addr(sprog) + 16u;
+            const uint32_t gate_s = seg_s + (uint32_t)((hd.x * sizeof(DevSeg) + 15) & ~size_t(15));
+            for (int si = 0; si < hd.x; ++si) {
+                run_segment<float, RB, NCB, 1>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)), gate_s, threadIdx.x,
+                                               c_swz64, ce);
+                __syncthreads();
+            }
+            poff += (uint32_t)hd.z;
         }
-        for (int e = threadIdx.x; e < (1 << ce); e += NCB) {
-            const int r = e >> low, l = e & ((1 << low) - 1);
-            const int64_t gidx = obase | deposit(r, op.high, op.nhigh) | l;
-            __stcg(amp + gidx, chunk[slot(e)]);
+#pragma unroll 4
+        for (int f = threadIdx.x; f < npairs; f += NCB) {
+            const int e = 2 * f;
+            const int64_t gidx = obase | s_dep[e >> low] | (e & lmask);
+            __stcg(reinterpret_cast<float4 *>(amp + gidx), *reinterpret_cast<const float4 *>(chunk + e));
         }
         __threadfence();
         __syncthreads();
@@ -236,7 +175,8 @@ __global__ void __launch_bounds__(NCB) k_batch(const BatchOp *__restrict__ ops, 
 }  // namespace
 
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
-                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int *dev_err, cudaStream_t st) {
+                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int *dev_err,
+                  cudaStream_t st) {
     const size_t smem = (size_t(1) << kBatchMaxChunkBits) * sizeof(float2) + kBatchMaxProgBytes;
     check_cuda(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(batch)");
@@ -247,7 +187,7 @@ void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *co
     const int grid = num_sms() * per_sm;
     k_batch<<<grid, NCB, smem, st>>>((const BatchOp *)dev_ops, nops, (const unsigned char *)dev_progs,
                                      (float2 *const *)dev_amps, dev_ops_done, dev_chunks_done, dev_next, total,
-                                     dev_err);
+                                     from_zero, dev_err);
     check_cuda(cudaGetLastError(), "batch kernel launch");
 }
 

@@ -36,12 +36,12 @@ __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate
     for (int gi = sg.g0; gi < sg.g1; ++gi) {
         const DevGate<double> &g = gates[gi];
         const int a = g.a;
-        if (g.op == OP_DENSE1 || g.op == OP_DIAG1) {
+        if (g.op == OP_DENSE1 || g.op == OP_DIAG1 || g.op == OP_X1) {
             for (int x = 0; x < 16; ++x) {
                 if (x & (1 << a)) continue;
                 const int y = x | (1 << a);
                 double m[8];
-                if (g.op == OP_DENSE1) {
+                if (g.op != OP_DIAG1) {
                     for (int k = 0; k < 8; ++k) m[k] = g.m[k];
                 } else {
                     m[0] = g.m[0]; m[1] = g.m[1]; m[2] = 0; m[3] = 0;

@@ -371,7 +371,10 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
             out.m[0] = (T)g.m[0]; out.m[1] = (T)g.m[1];
             out.m[2] = (T)g.m[6]; out.m[3] = (T)g.m[7];
         } else {
-            out.op = OP_DENSE1;
+            static const double kX[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+            bool flip = true;
+            for (int i = 0; i < 8; ++i) flip = flip && g.m[i] == kX[i];
+            out.op = flip ? OP_X1 : OP_DENSE1;
             for (int i = 0; i < 8; ++i) out.m[i] = (T)g.m[i];
         }
         return;
@@ -412,11 +415,14 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
             out.m[2 * r + 1] = (T)mm[2 * (r * 4 + r) + 1];
         }
     } else if (perm) {
-        out.op = OP_PERM2;
         // m[r] = source column of output row r
+        int pm[4] = {0, 0, 0, 0};
         for (int r = 0; r < 4; ++r)
             for (int cc = 0; cc < 4; ++cc)
-                if (mm[2 * (r * 4 + cc)] == 1.0) out.m[r] = (T)cc;
+                if (mm[2 * (r * 4 + cc)] == 1.0) pm[r] = cc;
+        for (int r = 0; r < 4; ++r) out.m[r] = (T)pm[r];
+        auto is = [&](int a0, int a1, int a2, int a3) { return pm[0] == a0 && pm[1] == a1 && pm[2] == a2 && pm[3] == a3; };
+        out.op = is(0, 3, 2, 1) ? OP_CXA : is(0, 1, 3, 2) ? OP_CXB : is(0, 2, 1, 3) ? OP_SWAP2 : OP_PERM2;
     } else {
         out.op = OP_DENSE2;
         for (int i = 0; i < 32; ++i) out.m[i] = (T)mm[i];

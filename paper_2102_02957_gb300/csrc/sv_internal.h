@@ -74,8 +74,16 @@ constexpr int MAX_SEG_BITS = 5;
 constexpr int kSwz64[24] = {SV_SWZ64_LIST};
 constexpr int kSwz128[24] = {SV_SWZ128_LIST};
 
-// Gate op-codes inside a segment.
-enum : int32_t { OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG1 = 2, OP_DIAG2 = 3, OP_PERM2 = 4 };
+// Gate op-codes inside a segment.  The exchange codes (bit flip, the two CNOT orientations,
+// SWAP) also carry their general form in m[] (dense 2x2 for OP_X1, the permutation of OP_PERM2
+// for the others) for consumers that do not special-case them.
+enum : int32_t {
+    OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG1 = 2, OP_DIAG2 = 3, OP_PERM2 = 4,
+    OP_CXA = 5,    // exchange local states 1 <-> 3: control = lower bit a, target = b
+    OP_CXB = 6,    // exchange 2 <-> 3: control = b, target = a
+    OP_SWAP2 = 7,  // exchange 1 <-> 2
+    OP_X1 = 8      // 1-qubit bit flip
+};
 
 // Register group as the kernel reads it.  A thread's group index g enumerates the chunk bits
 // outside the group: g bits 0..4 land on lane[0..4], the higher bits on rest[0..nrest).
@@ -148,12 +156,13 @@ constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x
 
 // Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
 // k < low (the contiguous low run of the chunk) and high[k - low] above it; the chunk index
-// enumerates the state bits outside the chunk, outer[] ascending.
+// enumerates the state bits outside the chunk, outer[] ascending.  The section's program is
+// npiece consecutive pieces at prog_off, each {nseg, ngate, bytes, 0} + DevSeg[] + DevGate[].
 struct BatchOp {
     int32_t state, op, ce, low;
     int64_t nchunks, first;  // chunks of this section; first global work-item index
     uint32_t prog_off, prog_bytes;
-    int32_t nseg, ngate;
+    int32_t npiece, pad;
     int32_t nhigh, nouter;
     int8_t high[24];
     int8_t outer[40];
@@ -161,7 +170,8 @@ struct BatchOp {
 constexpr int kBatchMaxChunkBits = 13;
 constexpr int kBatchMaxProgBytes = 24 * 1024;
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
-                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int *dev_err, cudaStream_t st);
+                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int *dev_err,
+                  cudaStream_t st);
 void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernels (launchers)

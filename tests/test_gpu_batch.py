@@ -57,7 +57,7 @@ def test_batch_small_states_one_residency(sv, use_graph):
     """States of 6..13 qubits fit one 13-bit chunk: one section each, the whole circuit in one
     shared-memory residency."""
     ns, descs = _workload([6, 7, 9, 11, 12, 13, 8, 10], 12, 0.05, 11, hea_n=10, hea_sets=3)
-    out, (items, sections) = _run_batch(sv, ns, descs, use_graph, repeats=2, chunk_bits=13)
+    out, (items, sections, _) = _run_batch(sv, ns, descs, use_graph, repeats=2, chunk_bits=13)
     assert sections >= len(ns)
     for n, d, got in zip(ns, descs, out):
         assert_close(got, sim.simulate(n, d), "c64")
@@ -68,7 +68,7 @@ def test_batch_multi_section_states(sv, use_graph):
     """States larger than the chunk: several gathered sections per state, ordered by the
     per-state completion counters inside one launch."""
     ns, descs = _workload([14, 16, 12, 18, 15], 20, 0.01, 5, hea_n=16, hea_sets=2)
-    out, (items, sections) = _run_batch(sv, ns, descs, use_graph, repeats=2, chunk_bits=10)
+    out, (items, sections, _) = _run_batch(sv, ns, descs, use_graph, repeats=2, chunk_bits=10)
     assert sections > len(ns)
     for n, d, got in zip(ns, descs, out):
         assert_close(got, sim.simulate(n, d), "c64")
@@ -110,3 +110,55 @@ def test_autotune_returns_a_valid_fast_choice(sv):
         st.apply(gates, sv.Plan(n, gates, **best))
         st.synchronize()
         assert_close(st.get_state(), sim.simulate(n, desc), "c64")
+
+
+def test_batch_tune_then_run(sv):
+    """The batch tuner picks chunk bits by timing runs on the states; re-initialised states then
+    give the oracle's result with the chosen options, and the byte count matches the sweeps."""
+    ns, descs = _workload([12, 15, 17, 14], 16, 1e-2, 9, hea_n=16, hea_sets=2)
+    gates = [sv.make_gates(d) for d in descs]
+    states = [sv.StateVector(n, "c64") for n in ns]
+    try:
+        for s in states:
+            s.init_basis(0)
+        best, ms = sv.batch_tune(states, gates)
+        assert ms > 0 and 10 <= best["chunk_bits"] <= 13
+        b = sv.Batch(states, gates, **best)
+        items, sections, nbytes = b.info()
+        assert nbytes >= 16.0 * sum(2 ** n for n in ns)
+        for s in states:
+            s.init_basis(0)
+        b.run(use_graph=True)
+        b.synchronize()
+        b.close()
+        for n, d, s in zip(ns, descs, states):
+            assert_close(s.get_state(), sim.simulate(n, d), "c64")
+    finally:
+        for s in states:
+            s.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_from_zero_ignores_prior_contents(sv, use_graph):
+    """SV_BATCH_FROM_ZERO: the first section synthesises |0..0>, so whatever the buffers held
+    before does not matter; a state with an empty gate list is reset to |0..0>."""
+    ns, descs = _workload([9, 14, 16, 13], 14, 2e-2, 21, hea_n=12, hea_sets=1)
+    ns.append(7)
+    descs.append([])
+    gates = [sv.make_gates(d) for d in descs]
+    rng = np.random.Generator(np.random.PCG64(5))
+    states = [sv.StateVector(n, "c64") for n in ns]
+    try:
+        b = sv.Batch(states, gates, chunk_bits=11)
+        for rep in range(2):
+            for n, s in zip(ns, states):
+                junk = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)).astype(np.complex64)
+                s.set_state(junk)
+            b.run(use_graph=use_graph, from_zero=True)
+            b.synchronize()
+        b.close()
+        for n, d, s in zip(ns, descs, states):
+            assert_close(s.get_state(), sim.simulate(n, d), "c64")
+    finally:
+        for s in states:
+            s.close()

@@ -123,3 +123,16 @@ def test_planner_schedule_parity_gathered(sv, n, c, pinned):
         q = planner.plan_blocking(n, desc, c, pinned=pinned)
         assert p.serialize() == q.serialize()
         assert p.info().n_swap_rounds == 0
+
+
+def test_binding_constants_match_header():
+    """Every enumerator `SV_NAME = value` in include/sv.h has the same value in the binding."""
+    import re
+    from paper_2102_02957_gb300 import _lib
+    with open(os.path.join(ROOT, "include", "sv.h")) as f:
+        text = f.read()
+    found = dict((k, int(v)) for k, v in re.findall(r"\b(SV_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert "SV_BATCH_FROM_ZERO" in found and "SV_ERR_TIMEOUT" in found
+    for name, value in found.items():
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == value, name
