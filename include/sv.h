@@ -78,7 +78,7 @@ typedef struct sv_options {
     int32_t restore_layout; /* 1: end with the output reordering of Sec. IV.C (Fig. 10 (b)). default 1 */
     int32_t seg_bits;       /* register-group width used inside a chunk (4); fusion width on TC path */
     int32_t use_tc;         /* 1: apply fused groups as 3xTF32 tensor-core contractions (complex64) */
-    int32_t use_model;      /* 1: let a trained cost model steer QB_CHUNK choices (sv_costmodel_*) */
+    int32_t use_model;      /* informational: 1 in plans made by sv_plan_blocking_steered; ignored as input */
     int32_t threads;        /* consumer threads per chunk CTA; 0 = auto                             */
     int32_t gather_pinned;  /* 0: the paper's chunk_swap rounds make every chunk bits 0..c-1.  p > 0:
                                gathered chunks -- a chunk is the low p bits plus c-p chosen bits,
@@ -117,8 +117,8 @@ sv_status sv_synchronize(sv_handle h);
 typedef struct sv_plan *sv_plan_h;
 
 /* Cache-blocking transpiler of Sec. IV.A (Listing 3) on the host.  Deterministic: the same
- * input gives the same schedule.  Uses opts->chunk_bits, reserve, restore_layout (and
- * use_model if a cost model is loaded).  SV_ERR_ARG when a gate is wider than the chunk. */
+ * input gives the same schedule.  Uses opts->chunk_bits, reserve, restore_layout, seg_bits,
+ * use_tc and gather_pinned.  SV_ERR_ARG when a gate is wider than the chunk. */
 sv_status sv_plan_blocking(int32_t n, const sv_gate *gates, int64_t n_gates,
                            const sv_options *opts, sv_plan_h *out);
 sv_status sv_plan_free(sv_plan_h plan);
@@ -214,6 +214,70 @@ sv_status sv_batch_tune(int32_t count, const sv_handle *states, const sv_gate *c
  * and frees its own scratch state; synchronises the device. */
 sv_status sv_autotune(int32_t n, int32_t dtype, const sv_gate *gates, int64_t n_gates, const sv_options *base,
                       sv_options *best, double *best_ms);
+
+/* ------------------------------------------------------------------ learned cost model */
+/* The paper's QB_CHUNK rule (Sec. IV.A) is a fixed heuristic; the paper notes that better
+ * schedules exist but gives no method (it has no counterpart of this section).  The library adds
+ * a small regression network that predicts the kernel time of a blocking section from 16
+ * features of it, trained on timings the library measures itself, and a planner variant in
+ * which the prediction picks each section's chunk among candidates: the paper's rule (always
+ * candidate 0), the rule with one or two fewer chunk qubits, and a look-ahead set that takes the
+ * most gates.  Gathered chunks (gather_pinned > 0) only.  Every candidate is a valid section,
+ * so no amplitude depends on the model.
+ *
+ * Network: x (16) -> relu(W1 x + b1) (64) -> relu(W2 h1 + b2) (64) -> y = w3 . h2 + b3, FP32;
+ * y estimates the standardised log of the section's kernel microseconds.  Parameters, flat
+ * (5313 floats): W1 (64 x 16, row-major), b1 (64), W2 (64 x 64, row-major), b2 (64), w3 (64),
+ * b3.  Training: mean squared error, Adam (b1 0.9, b2 0.999, eps 1e-8) on the GPU by the
+ * library's own forward / backward / update kernels.  A model lives on the device that was
+ * current at creation; its calls synchronise. */
+typedef struct sv_costmodel *sv_costmodel_h;
+enum { SV_COSTMODEL_FEATURES = 16, SV_COSTMODEL_PARAMS = 5313 };
+/* He-uniform weights (bound sqrt(6 / fan_in)) from a SplitMix64 stream seeded with `seed`,
+ * zero biases, empty sample set. */
+sv_status sv_costmodel_create(uint64_t seed, sv_costmodel_h *out);
+sv_status sv_costmodel_free(sv_costmodel_h m);
+/* Copy the flat parameters out / in (count must be SV_COSTMODEL_PARAMS); setting them clears
+ * the Adam moments and step count. */
+sv_status sv_costmodel_get_params(sv_costmodel_h m, float *out, int64_t count);
+sv_status sv_costmodel_set_params(sv_costmodel_h m, const float *in, int64_t count);
+/* Raw network outputs y for `count` host feature rows (count x 16, row-major) -> host out. */
+sv_status sv_costmodel_forward(sv_costmodel_h m, const float *x, int64_t count, float *y);
+/* Gradient of L = (1/count) sum (y_i - t_i)^2 at the current parameters (host in, host out:
+ * grad has SV_COSTMODEL_PARAMS entries) and L itself. */
+sv_status sv_costmodel_gradient(sv_costmodel_h m, const float *x, const float *t, int64_t count, float *grad,
+                                double *loss);
+/* One Adam step on this batch (raw targets t); loss receives L before the step. */
+sv_status sv_costmodel_adam_step(sv_costmodel_h m, const float *x, const float *t, int64_t count, float lr,
+                                 double *loss);
+/* Training samples: feature rows and measured section times in microseconds. */
+sv_status sv_costmodel_add_samples(sv_costmodel_h m, const float *x, const float *us, int64_t count);
+sv_status sv_costmodel_num_samples(sv_costmodel_h m, int64_t *count);
+/* Timing collector: for each of the n_opts option sets, plan the circuit (candidate sections
+ * picked at random from a SplitMix64 stream seeded with policy_seed + k when policy_seed != 0,
+ * else the paper's rule), apply it to h twice (the second timed per launch with CUDA events)
+ * and add one sample per blocking section.  Overwrites h's amplitudes. */
+sv_status sv_costmodel_collect(sv_costmodel_h m, sv_handle h, const sv_gate *gates, int64_t n_gates,
+                               const sv_options *opts, int32_t n_opts, uint64_t policy_seed, int64_t *added);
+/* Train on all samples: targets standardised log(us); `epochs` passes of shuffled minibatches
+ * of `batch` samples (SplitMix64 shuffle seeded with `seed`), Adam with rate lr.  mse receives
+ * the final mean squared error of log(us) over the samples. */
+sv_status sv_costmodel_train(sv_costmodel_h m, int32_t epochs, int32_t batch, float lr, uint64_t seed, double *mse);
+/* Predicted section kernel time in microseconds for `count` feature rows. */
+sv_status sv_costmodel_predict_us(sv_costmodel_h m, const float *x, int64_t count, float *us);
+/* Features of every blocking section of a plan, in plan order (rows x 16); rows receives the
+ * number of sections (at most max_rows are written). */
+sv_status sv_costmodel_features(sv_plan_h plan, const sv_gate *gates, int32_t dtype, float *out, int64_t max_rows,
+                                int64_t *rows);
+/* Planner with the model's steering (see above): per section, the candidate with the most gates
+ * per predicted microsecond.  Same constraints and output as sv_plan_blocking; requires
+ * opts->gather_pinned > 0 and a trained model. */
+sv_status sv_plan_blocking_steered(int32_t n, const sv_gate *gates, int64_t n_gates, const sv_options *opts,
+                                   int32_t dtype, sv_costmodel_h model, sv_plan_h *out);
+/* Per-launch device times of the last sv_apply_circuit with profiling on: kind (0 per-gate,
+ * 1 blocking section, 2 permutation), plan op index (-1 per-gate), milliseconds.  count
+ * receives the number of launches (at most max entries are written).  Synchronises. */
+sv_status sv_get_launch_times(sv_handle h, int32_t *kind, int32_t *op_index, float *ms, int64_t max, int64_t *count);
 
 /* ------------------------------------------------------------------ readouts (FP64 accumulate) */
 /* Measurement probabilities |a_i|^2 (Sec. II.A) for all 2^n indices.  out: 2^n doubles,

@@ -52,12 +52,26 @@ def options(**kw) -> sv_options:
 
 
 class Plan:
-    """A cache-blocking schedule made by the library's planner (sv_plan_blocking)."""
+    """A cache-blocking schedule made by the library's planner (sv_plan_blocking), or, with a
+    trained CostModel, by the steered planner (sv_plan_blocking_steered)."""
 
-    def __init__(self, n: int, gates: np.ndarray, **opts):
+    def __init__(self, n: int, gates: np.ndarray, model: "CostModel | None" = None, dtype="c64", **opts):
         self._h = ctypes.c_void_p()
         o = options(**opts)
-        check(lib().sv_plan_blocking(n, gates.ctypes.data, len(gates), ctypes.byref(o), ctypes.byref(self._h)))
+        if model is None:
+            check(lib().sv_plan_blocking(n, gates.ctypes.data, len(gates), ctypes.byref(o), ctypes.byref(self._h)))
+        else:
+            check(lib().sv_plan_blocking_steered(n, gates.ctypes.data, len(gates), ctypes.byref(o), DTYPES[dtype],
+                                                 model._h, ctypes.byref(self._h)))
+
+    def features(self, gates: np.ndarray, dtype="c64") -> np.ndarray:
+        """Cost-model features of every blocking section (sv_costmodel_features)."""
+        rows = ctypes.c_int64()
+        check(lib().sv_costmodel_features(self._h, gates.ctypes.data, DTYPES[dtype], None, 0, ctypes.byref(rows)))
+        out = np.zeros((rows.value, _lib.SV_COSTMODEL_FEATURES), dtype=np.float32)
+        check(lib().sv_costmodel_features(self._h, gates.ctypes.data, DTYPES[dtype], out.ctypes.data, rows.value,
+                                          ctypes.byref(rows)))
+        return out
 
     @property
     def handle(self):
@@ -131,6 +145,17 @@ class StateVector:
 
     def set_profiling(self, on: bool = True):
         check(lib().sv_set_profiling(self._h, int(bool(on))))
+
+    def launch_times(self):
+        """(kind, plan op index, milliseconds) per launch of the last profiled apply."""
+        cnt = ctypes.c_int64()
+        check(lib().sv_get_launch_times(self._h, None, None, None, 0, ctypes.byref(cnt)))
+        k = np.zeros(cnt.value, dtype=np.int32)
+        o = np.zeros(cnt.value, dtype=np.int32)
+        ms = np.zeros(cnt.value, dtype=np.float32)
+        check(lib().sv_get_launch_times(self._h, k.ctypes.data, o.ctypes.data, ms.ctypes.data, cnt.value,
+                                        ctypes.byref(cnt)))
+        return k, o, ms
 
     def stats(self) -> sv_apply_stats:
         s = sv_apply_stats()
@@ -256,3 +281,84 @@ def autotune(n: int, gates: np.ndarray, dtype="c64", **base):
     check(lib().sv_autotune(n, DTYPES[dtype], gates.ctypes.data, len(gates), ctypes.byref(b), ctypes.byref(best),
                             ctypes.byref(ms)))
     return {k: getattr(best, k) for k in _OPT_KEYS}, ms.value
+
+
+class CostModel:
+    """The learned section-time model (sv_costmodel_*): GPU training and inference kernels."""
+
+    NF = _lib.SV_COSTMODEL_FEATURES
+    NP = _lib.SV_COSTMODEL_PARAMS
+
+    def __init__(self, seed: int = 0):
+        self._h = ctypes.c_void_p()
+        check(lib().sv_costmodel_create(seed, ctypes.byref(self._h)))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.NP, dtype=np.float32)
+        check(lib().sv_costmodel_get_params(self._h, out.ctypes.data, self.NP))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(lib().sv_costmodel_set_params(self._h, p.ctypes.data, p.size))
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.NF)
+        y = np.zeros(len(x), dtype=np.float32)
+        check(lib().sv_costmodel_forward(self._h, x.ctypes.data, len(x), y.ctypes.data))
+        return y
+
+    def gradient(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.NF)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.NP, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(lib().sv_costmodel_gradient(self._h, x.ctypes.data, t.ctypes.data, len(x), g.ctypes.data,
+                                          ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, x, t, lr: float) -> float:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.NF)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(lib().sv_costmodel_adam_step(self._h, x.ctypes.data, t.ctypes.data, len(x), lr, ctypes.byref(loss)))
+        return loss.value
+
+    def add_samples(self, x, us) -> None:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.NF)
+        us = np.ascontiguousarray(us, dtype=np.float32)
+        check(lib().sv_costmodel_add_samples(self._h, x.ctypes.data, us.ctypes.data, len(x)))
+
+    def num_samples(self) -> int:
+        c = ctypes.c_int64()
+        check(lib().sv_costmodel_num_samples(self._h, ctypes.byref(c)))
+        return c.value
+
+    def collect(self, state: StateVector, gates: np.ndarray, option_sets, policy_seed: int = 0) -> int:
+        arr = (sv_options * len(option_sets))(*[options(**o) for o in option_sets])
+        added = ctypes.c_int64()
+        check(lib().sv_costmodel_collect(self._h, state._h, gates.ctypes.data, len(gates), arr, len(option_sets),
+                                         policy_seed, ctypes.byref(added)))
+        return added.value
+
+    def train(self, epochs: int = 200, batch: int = 256, lr: float = 1e-3, seed: int = 1) -> float:
+        mse = ctypes.c_double()
+        check(lib().sv_costmodel_train(self._h, epochs, batch, lr, seed, ctypes.byref(mse)))
+        return mse.value
+
+    def predict_us(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.NF)
+        us = np.zeros(len(x), dtype=np.float32)
+        check(lib().sv_costmodel_predict_us(self._h, x.ctypes.data, len(x), us.ctypes.data))
+        return us
+
+    def close(self):
+        if self._h:
+            lib().sv_costmodel_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

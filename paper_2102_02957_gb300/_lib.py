@@ -56,6 +56,8 @@ _lib = None
 # name -> (restype, argtypes)
 SV_BATCH_GRAPH = 1
 SV_BATCH_FROM_ZERO = 2
+SV_COSTMODEL_FEATURES = 16
+SV_COSTMODEL_PARAMS = 5313
 _VP = ctypes.c_void_p
 _SIGS = {
     "sv_gate_make": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _VP]),
@@ -89,6 +91,26 @@ _SIGS = {
     "sv_batch_free": (ctypes.c_int, [_VP]),
     "sv_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(sv_options),
                                    ctypes.POINTER(sv_options), ctypes.POINTER(ctypes.c_double)]),
+    "sv_costmodel_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_VP)]),
+    "sv_costmodel_free": (ctypes.c_int, [_VP]),
+    "sv_costmodel_get_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "sv_costmodel_set_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
+    "sv_costmodel_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
+    "sv_costmodel_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "sv_costmodel_adam_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
+                                              ctypes.POINTER(ctypes.c_double)]),
+    "sv_costmodel_add_samples": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
+    "sv_costmodel_num_samples": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "sv_costmodel_collect": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_uint64,
+                                            ctypes.POINTER(ctypes.c_int64)]),
+    "sv_costmodel_train": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "sv_costmodel_predict_us": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
+    "sv_costmodel_features": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "sv_plan_blocking_steered": (ctypes.c_int, [ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(sv_options),
+                                                ctypes.c_int32, _VP, ctypes.POINTER(_VP)]),
+    "sv_get_launch_times": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sv_last_error": (ctypes.c_char_p, []),
 }
 

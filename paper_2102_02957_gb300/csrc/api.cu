@@ -439,7 +439,7 @@ sv_status sv_plan_serialize(sv_plan_h p, int64_t *buf, int64_t cap, int64_t *len
 }
 
 // Timing marks around launches (profiling mode): kind 0 = per-gate, 1 = block, 2 = permute.
-static void mark_begin(sv_state *h, int kind) {
+static void mark_begin(sv_state *h, int kind, int op = -1) {
     if (!h->profiling) return;
     const size_t need = 2 * (h->ev_marks.size() + 1);
     while (h->ev_pool.size() < need) {
@@ -449,12 +449,12 @@ static void mark_begin(sv_state *h, int kind) {
     }
     const int idx = (int)(2 * h->ev_marks.size());
     check_cuda(cudaEventRecord(h->ev_pool[idx], h->stream), "cudaEventRecord");
-    h->ev_marks.emplace_back(kind, idx);
+    h->ev_marks.push_back(sv_state::Mark{kind, idx, op});
 }
 
 static void mark_end(sv_state *h) {
     if (!h->profiling) return;
-    check_cuda(cudaEventRecord(h->ev_pool[h->ev_marks.back().second + 1], h->stream), "cudaEventRecord");
+    check_cuda(cudaEventRecord(h->ev_pool[h->ev_marks.back().ev + 1], h->stream), "cudaEventRecord");
 }
 
 sv_status sv_set_profiling(sv_handle h, int32_t on) {
@@ -511,7 +511,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
             if (op.kind == 2 || op.kind == 4) {
                 for (; bi < progs.size() && progs[bi].op_index == (int)oi; ++bi) {
                     const BlockProg &bp = progs[bi];
-                    mark_begin(h, 1);
+                    mark_begin(h, 1, (int)oi);
                     if (tc)
                         launch_block_tc(h->amp, h->n, plan->c, bp.gathered ? &bp.lay : nullptr, base + bp.off, bp.nseg,
                                         h->dev_err, h->stream);
@@ -527,7 +527,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
                 }
                 continue;
             } else {
-                mark_begin(h, 2);
+                mark_begin(h, 2, (int)oi);
                 launch_permute(h->dtype, h->amp, h->n, op.pairs, h->stream);
                 mark_end(h);
                 ++st.sweeps_permute;
@@ -546,11 +546,10 @@ sv_status sv_get_apply_stats(sv_handle h, sv_apply_stats *out) {
     if (h->profiling && !h->ev_marks.empty() && !h->stats_timed) {
         check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         double ms[3] = {0, 0, 0};
-        for (auto km : h->ev_marks) {
+        for (const auto &km : h->ev_marks) {
             float t = 0;
-            check_cuda(cudaEventElapsedTime(&t, h->ev_pool[km.second], h->ev_pool[km.second + 1]),
-                       "cudaEventElapsedTime");
-            ms[km.first] += t;
+            check_cuda(cudaEventElapsedTime(&t, h->ev_pool[km.ev], h->ev_pool[km.ev + 1]), "cudaEventElapsedTime");
+            ms[km.kind] += t;
         }
         h->stats.ms_gate = ms[0];
         h->stats.ms_block = ms[1];
@@ -558,6 +557,23 @@ sv_status sv_get_apply_stats(sv_handle h, sv_apply_stats *out) {
         h->stats_timed = true;
     }
     *out = h->stats;
+    SV_API_END
+}
+
+sv_status sv_get_launch_times(sv_handle h, int32_t *kind, int32_t *op_index, float *ms, int64_t max, int64_t *count) {
+    SV_API_BEGIN
+    if (!h || !count) fail(SV_ERR_ARG, "null argument");
+    if (!h->profiling) fail(SV_ERR_ARG, "profiling is off");
+    check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    *count = (int64_t)h->ev_marks.size();
+    for (int64_t k = 0; k < *count && k < max; ++k) {
+        const auto &km = h->ev_marks[(size_t)k];
+        float t = 0;
+        check_cuda(cudaEventElapsedTime(&t, h->ev_pool[km.ev], h->ev_pool[km.ev + 1]), "cudaEventElapsedTime");
+        if (kind) kind[k] = km.kind;
+        if (op_index) op_index[k] = km.op;
+        if (ms) ms[k] = t;
+    }
     SV_API_END
 }
 

@@ -14,6 +14,7 @@
 //  * SWAP gates are relabels; the final reordering is a bit permutation split into two rounds
 //    of disjoint transpositions.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 
@@ -23,7 +24,8 @@ namespace sv {
 
 static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
 
-sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o) {
+sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o, SectionChooser *chooser,
+                       int dtype) {
     if (n < 1 || n > 62) fail(SV_ERR_ARG, "n out of range");
     if (n_gates < 0 || (n_gates > 0 && !gates)) fail(SV_ERR_ARG, "null gate list");
     const int c = o.chunk_bits;
@@ -87,14 +89,13 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     std::iota(m.begin(), m.end(), 0);
     std::iota(pinv.begin(), pinv.end(), 0);
 
-    std::vector<PG> next;
-    while (!remaining.empty()) {
-        // choose QB_CHUNK
+    // The paper's QB_CHUNK rule for a chunk of `tgt` qubits.
+    auto rule_select = [&](int tgt) {
         uint64_t chosen = 0;
         int cnt = 0;
         auto try_add = [&](uint64_t msk) {
             const uint64_t fresh = msk & ~chosen;
-            if (cnt + popc(fresh) <= target) {
+            if (cnt + popc(fresh) <= tgt) {
                 chosen |= fresh;
                 cnt += popc(fresh);
             }
@@ -102,14 +103,99 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         for (int p = 0; p < pinned; ++p) try_add(1ull << pinv[p]);  // gathered chunks keep the low bits
         try_add(remaining.front().vmask);
         for (const PG &g : remaining) {
-            if (cnt >= target) break;
+            if (cnt >= tgt) break;
             if (g.nq > 1) try_add(g.vmask);
         }
         for (const PG &g : remaining) {
-            if (cnt >= target) break;
+            if (cnt >= tgt) break;
             if (g.nq == 1) try_add(g.vmask);
         }
-        for (int p = 0; p < (pinned ? n : width) && cnt < target; ++p) try_add(1ull << pinv[p]);
+        for (int p = 0; p < (pinned ? n : width) && cnt < tgt; ++p) try_add(1ull << pinv[p]);
+        return chosen;
+    };
+    // Gates of REMAINING (at most `limit` inspected) that a section on `chosen` would take.
+    auto absorbed = [&](uint64_t chosen, size_t limit) {
+        uint64_t blocked = 0;
+        int k = 0;
+        for (size_t i = 0; i < remaining.size() && i < limit; ++i) {
+            const PG &g = remaining[i];
+            if ((g.vmask & ~chosen) == 0 && (g.vmask & blocked) == 0) ++k;
+            else if (g.vmask & chosen) blocked |= g.vmask;
+        }
+        return k;
+    };
+    // Look-ahead alternative (cost-model candidates only): grow the chunk from the pinned bits
+    // and the first gate by the pending gate whose qubits add the most absorbable gates.
+    auto greedy_select = [&](int tgt) {
+        constexpr size_t kWindow = 512, kChoices = 64;
+        uint64_t chosen = remaining.front().vmask;
+        for (int p = 0; p < pinned; ++p) chosen |= 1ull << pinv[p];
+        while (popc(chosen) < tgt) {
+            uint64_t best = 0;
+            int best_score = -1;
+            size_t tried = 0;
+            std::vector<uint64_t> seen;
+            for (size_t i = 0; i < remaining.size() && i < kWindow && tried < kChoices; ++i) {
+                const uint64_t fresh = remaining[i].vmask & ~chosen;
+                if (!fresh || popc(chosen | fresh) > tgt) continue;
+                if (std::find(seen.begin(), seen.end(), fresh) != seen.end()) continue;
+                seen.push_back(fresh);
+                ++tried;
+                const int sc = absorbed(chosen | fresh, kWindow);
+                if (sc > best_score) {
+                    best_score = sc;
+                    best = fresh;
+                }
+            }
+            if (!best) break;
+            chosen |= best;
+        }
+        for (int p = 0; p < n && popc(chosen) < tgt; ++p) chosen |= 1ull << pinv[p];
+        return chosen;
+    };
+
+    std::vector<PG> next;
+    std::vector<SectionCandidate> cands;
+    while (!remaining.empty()) {
+        // choose QB_CHUNK
+        uint64_t chosen = rule_select(target);
+        if (chooser && pinned) {
+            cands.clear();
+            auto add_candidate = [&](uint64_t ch) {
+                for (const SectionCandidate &c0 : cands)
+                    if (c0.chosen == ch) return;
+                SectionCandidate cd;
+                cd.chosen = ch;
+                cd.ce = popc(ch);
+                PlanOp tmp;
+                tmp.kind = 4;
+                uint64_t blocked = 0;
+                for (const PG &g : remaining) {
+                    if ((g.vmask & ~ch) == 0 && (g.vmask & blocked) == 0) {
+                        BlockGate bg{};
+                        bg.gi = g.gi;
+                        bg.nq = g.nq;
+                        for (int j = 0; j < g.nq; ++j) bg.phys[j] = m[g.vq[j]];
+                        if (g.nq == 1) bg.phys[1] = -1;
+                        tmp.gates.push_back(bg);
+                    } else if (g.vmask & ch) {
+                        blocked |= g.vmask;
+                    }
+                }
+                for (int v = 0; v < n; ++v)
+                    if ((ch >> v) & 1) tmp.mask |= 1ull << m[v];
+                cd.absorbed = (int)tmp.gates.size();
+                section_features(*plan, tmp, gates, dtype, cd.f);
+                cands.push_back(cd);
+            };
+            add_candidate(chosen);
+            // smaller chunks (still room for a 2-qubit gate; >= 11 bits for the tensor-core path)
+            const int min_t = std::max(pinned + 2, (o.use_tc && dtype == SV_C64) ? 11 : 1);
+            for (int d = 1; d <= 2; ++d)
+                if (target - d >= min_t && target - d >= remaining.front().nq + pinned) add_candidate(rule_select(target - d));
+            add_candidate(greedy_select(target));
+            chosen = cands[(size_t)std::max(0, std::min((int)cands.size() - 1, chooser->choose(cands)))].chosen;
+        }
 
         // chunk_swap round (none for gathered chunks: the section fetches its bits in place)
         PlanOp round;
@@ -427,6 +513,69 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
         out.op = OP_DENSE2;
         for (int i = 0; i < 32; ++i) out.m[i] = (T)mm[i];
     }
+}
+
+// A gate that costs no multiplication-heavy work: diagonal, or a permutation (entries 0 / 1).
+static bool gate_is_cheap(const sv_gate &g) {
+    const int d = 1 << g.nq;
+    bool diag = true, perm = true;
+    for (int r = 0; r < d; ++r) {
+        int ones = 0;
+        for (int c = 0; c < d; ++c) {
+            const double re = g.m[2 * (r * d + c)], im = g.m[2 * (r * d + c) + 1];
+            const bool zero = re == 0.0 && im == 0.0;
+            if (r != c && !zero) diag = false;
+            if (re == 1.0 && im == 0.0) ++ones;
+            else if (!zero) perm = false;
+        }
+        if (ones != 1) perm = false;
+    }
+    return diag || perm;
+}
+
+// Features of one blocking section for the cost model (all roughly in [0, 1]):
+//  0 chunk bits / 16          1 register-group width / 8     2 log2(1 + gates) / 10
+//  3 log2(1 + groups) / 6     4..9 share of gate-qubit chunk positions in bins {0},{1},{2},{3},
+//  {4..7},{8..}               10 share of 2-qubit gates       11 share of diagonal/permutation gates
+//  12 complex128              13 n / 32                       14 tensor-core sweeps / 4 (0 = SIMT)
+//  15 gathered chunk
+void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gates, int dtype, float *out) {
+    for (int k = 0; k < kNumFeatures; ++k) out[k] = 0.f;
+    const int n = plan.n;
+    std::vector<BlockGate> loc = op.gates;
+    int ce = std::min(plan.c, n);
+    if (op.kind == 4) {
+        const GatherLayout L = gather_layout(op.mask, n, 8);
+        for (BlockGate &g : loc)
+            for (int j = 0; j < g.nq; ++j) g.phys[j] = L.local_of[g.phys[j]];
+        ce = L.ce;
+    }
+    const bool tc = plan.use_tc && dtype == SV_C64 && ce >= 11;
+    const int r = tc ? 4 : (dtype == SV_C64 ? plan.seg_bits : 4);
+    const int nseg = loc.empty() ? 0 : (int)segment_block(loc, ce, r, 8).size();
+    int q_total = 0, two = 0, cheap = 0;
+    float hist[6] = {0, 0, 0, 0, 0, 0};
+    for (const BlockGate &g : loc) {
+        two += g.nq == 2;
+        cheap += gate_is_cheap(gates[g.gi]);
+        for (int j = 0; j < g.nq; ++j) {
+            const int p = g.phys[j];
+            hist[p < 4 ? p : (p < 8 ? 4 : 5)] += 1.f;
+            ++q_total;
+        }
+    }
+    const float ng = (float)loc.size();
+    out[0] = ce / 16.f;
+    out[1] = r / 8.f;
+    out[2] = std::log2(1.f + ng) / 10.f;
+    out[3] = std::log2(1.f + (float)nseg) / 6.f;
+    for (int b = 0; b < 6; ++b) out[4 + b] = q_total ? hist[b] / (float)q_total : 0.f;
+    out[10] = ng > 0 ? two / ng : 0.f;
+    out[11] = ng > 0 ? cheap / ng : 0.f;
+    out[12] = dtype == SV_C128 ? 1.f : 0.f;
+    out[13] = n / 32.f;
+    out[14] = tc ? (float)((nseg + 10) / 11) / 4.f : 0.f;
+    out[15] = op.kind == 4 ? 1.f : 0.f;
 }
 
 template void encode_gate<float>(const sv_gate &, const BlockGate &, const HostSeg &, DevGate<float> &);

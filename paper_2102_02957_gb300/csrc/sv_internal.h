@@ -59,7 +59,25 @@ struct sv_plan {
 
 namespace sv {
 
-sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o);
+// Cost-model steering of the transpiler's QB_CHUNK choice (gathered chunks only): for every
+// section the planner lists candidate chunk sets -- candidates[0] is always the paper's rule --
+// with the gates each would take and its features, and a chooser picks one.
+constexpr int kNumFeatures = 16;
+struct SectionCandidate {
+    uint64_t chosen = 0;  // qubits of the chunk
+    int absorbed = 0;     // gates the section takes
+    int ce = 0;           // chunk bits
+    float f[kNumFeatures] = {0};
+};
+struct SectionChooser {
+    virtual ~SectionChooser() = default;
+    virtual int choose(const std::vector<SectionCandidate> &cands) = 0;
+};
+
+sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_options &o,
+                       SectionChooser *chooser = nullptr, int dtype = SV_C64);
+// The 16 features of a blocking section (kind 2 or 4) as the cost model sees it.
+void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gates, int dtype, float *out);
 
 // ------------------------------------------------------------------ block programs
 constexpr int SEG_BITS = 4;      // default register-group width (amplitudes per group = 2^SEG_BITS)
@@ -174,6 +192,15 @@ void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *co
                   cudaStream_t st);
 void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st);
 
+// cost-model network kernels (k_mlp.cu)
+int mlp_param_count();
+int mlp_grad_blocks(int64_t B);
+void launch_mlp_fwd(const float *P, const float *X, int64_t B, float *Y, cudaStream_t st);
+void launch_mlp_grad(const float *P, const float *X, const float *T, const int32_t *idx, int64_t start, int64_t B,
+                     float *part, double *lpart, cudaStream_t st);
+void launch_mlp_reduce(const float *part, int nblk, const double *lpart, double *loss, int mode, float *grad, float *P,
+                       float *M, float *V, float lr, float c1, float c2, cudaStream_t st);
+
 // ------------------------------------------------------------------ kernels (launchers)
 struct Mat1 { float m[8]; };
 struct Mat2 { float m[32]; };
@@ -235,6 +262,9 @@ struct sv_state {
     int device = 0;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;                 // reusable timing events
-    std::vector<std::pair<int, int>> ev_marks;        // (kind, index of start event) per launch
+    struct Mark {
+        int kind, ev, op;  // launch kind, index of its start event, plan op (-1: per-gate)
+    };
+    std::vector<Mark> ev_marks;
     bool stats_timed = false;
 };

@@ -136,3 +136,19 @@ def test_binding_constants_match_header():
     for name, value in found.items():
         if hasattr(_lib, name):
             assert getattr(_lib, name) == value, name
+
+
+def test_section_features_hand_computed():
+    """Cost-model features of a one-section plan, worked out by hand (host code, no GPU)."""
+    import paper_2102_02957_gb300 as sv
+    desc = [("h", (0,), ()), ("cx", (0, 1), ()), ("cz", (2, 3), ())]
+    g = sv.make_gates(desc)
+    plan = sv.Plan(8, g, chunk_bits=6, gather_pinned=4)
+    f = plan.features(g, "c64")
+    assert f.shape == (1, 16)
+    want = np.array([6 / 16, 4 / 8, np.log2(4) / 10, np.log2(2) / 6,
+                     2 / 5, 1 / 5, 1 / 5, 1 / 5, 0, 0,        # qubit positions 0,0,1,2,3
+                     2 / 3, 2 / 3, 0, 8 / 32, 0, 1], dtype=np.float32)
+    np.testing.assert_allclose(f[0], want, rtol=1e-6, atol=1e-7)
+    f128 = plan.features(g, "c128")
+    assert f128[0, 12] == 1.0
