@@ -65,6 +65,11 @@ __device__ __forceinline__ int lds_s16(uint32_t a) {
     asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
+__device__ __forceinline__ int lds_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ void ldc_i4(uint32_t a, int &x, int &y, int &z, int &w) {
     asm("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
 }

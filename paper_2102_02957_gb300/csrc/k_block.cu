@@ -104,9 +104,15 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
     // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
     bool failed = false;
-    auto stage = [&](int t, int k, int &base, int &sbase) -> bool {
+    // The tensor cores' FP32 accumulation truncates, which shrinks every result by a few units
+    // in the last place -- a bias that compounds over hundreds of register groups.  For a
+    // unitary group the exact row keeps its norm, so each row of D is rescaled to the norm of its
+    // input row (the radial part of the error is removed; what remains is unbiased rounding).
+    const bool unitary = lds_s32(bhi + 8192) != 0;
+    auto stage = [&](int t, int k, int &base, int &sbase, float &nrm) -> bool {
         row_base(t, base, sbase);
         uint32_t ahi[32], alo[32];
+        nrm = 0.f;
         // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
         // buffer base is only 1 KiB aligned, so it is added after the XOR walk, never XORed
         uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
@@ -120,6 +126,7 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
             ahi[2 * gidx + 1] = __float_as_uint(xi);
             alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u));
             alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u));
+            nrm = fmaf(xr, xr, fmaf(xi, xi, nrm));
         }
         const uint32_t col = tcol + (uint32_t)k * 96;
         ptx::tmem_st32(col + lane_off, ahi);
@@ -147,7 +154,7 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     };
     // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
     // (after an expired wait the tile is garbage; the group stops at its next barrier)
-    auto finish = [&](int k, int base, int sbase) {
+    auto finish = [&](int k, int base, int sbase, float nrm) {
         if (!ptx::mbar_wait(&mbar[k], phase[k], kWaitLimitNs)) {
             failed = true;
             *abort_flag = 1;
@@ -157,6 +164,17 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         uint32_t y[32];
         ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
         ptx::tmem_wait_ld();
+        if (unitary) {
+            // y <- y (1 + d), d = sqrt(nrm / ny) - 1 ~ (nrm - ny) / (2 ny): applied as a small
+            // correction, since a scale factor rounded to FP32 next to 1 would itself be off by a
+            // nearly constant half unit in the last place for every row
+            float ny = 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) ny = fmaf(__uint_as_float(y[q]), __uint_as_float(y[q]), ny);
+            const float d = ny > 0.f ? 0.5f * (nrm - ny) / ny : 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) y[q] = __float_as_uint(fmaf(__uint_as_float(y[q]), d, __uint_as_float(y[q])));
+        }
         uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
 #pragma unroll
         for (int b = 0; b < NA; ++b) {
@@ -167,15 +185,18 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     };
     // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
     int pb, ps;
-    if (!stage(0, 0, pb, ps)) return false;
+    float pn;
+    if (!stage(0, 0, pb, ps, pn)) return false;
     for (int t = 1; t < T; ++t) {
         int nb, ns;
-        if (!stage(t, t & 1, nb, ns)) return false;
-        finish((t - 1) & 1, pb, ps);
+        float nn;
+        if (!stage(t, t & 1, nb, ns, nn)) return false;
+        finish((t - 1) & 1, pb, ps, pn);
         pb = nb;
         ps = ns;
+        pn = nn;
     }
-    finish((T - 1) & 1, pb, ps);
+    finish((T - 1) & 1, pb, ps, pn);
     return !ptx::named_bar_or(bar_id, NC, failed);  // the group leaves together
 }
 
@@ -199,6 +220,73 @@ __device__ __forceinline__ int64_t gather_origin(const GatherArgs &ga, int64_t j
     for (int k = 0; k < ga.nloop; ++k)
         if ((t >> k) & 1) x |= int64_t(1) << ga.loop[k];
     return x;
+}
+
+// Producer (one thread): stream this CTA's chunks j = blockIdx.x + it * gridDim.x into the ring
+// of nbuf shared-memory buffers (bulk copies for contiguous chunks, tensor copies for gathered
+// ones), each completing on full[slot]; a slot is reused once its consumer arrived on empty[slot].
+template <typename T2>
+__device__ __forceinline__ void produce_chunks(T2 *state, int c, int64_t count, int nbuf, T2 *bufs, uint64_t *full,
+                                               uint64_t *empty, volatile int *abort_flag, int *err,
+                                               const GatherArgs &ga, const CUtensorMap *tmap) {
+    const int chunk_amps = 1 << c;
+    const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
+    int64_t issued = 0;
+    for (int64_t it = 0; it < count; ++it) {
+        const int s = (int)(it % nbuf);
+        if (it >= nbuf) {
+            if (!ptx::mbar_wait(&empty[s], (uint32_t)((it / nbuf - 1) & 1), kWaitLimitNs) || *abort_flag) {
+                atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+                *abort_flag = 1;
+                break;
+            }
+        }
+        const int64_t j = blockIdx.x + it * gridDim.x;
+        unsigned char *dst = reinterpret_cast<unsigned char *>(bufs + (size_t)s * chunk_amps);
+        ptx::mbar_arrive_expect_tx(&full[s], chunk_bytes);
+        if (ga.rank > 0) {
+            for (int t = 0; t < (1 << ga.nloop); ++t) {
+                int coord[5];
+                gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
+                ptx::tensor_g2s(dst + (size_t)t * ga.box_amps * sizeof(T2), tmap, coord, ga.rank, &full[s]);
+            }
+        } else {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(state + j * chunk_amps);
+            for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+                const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
+                ptx::bulk_g2s(dst + o, src + o, b, &full[s]);
+            }
+        }
+        ++issued;
+    }
+    // do not leave while copies into this CTA's shared memory are still in flight
+    for (int64_t it = issued > nbuf ? issued - nbuf : 0; it < issued; ++it)
+        (void)ptx::mbar_wait(&full[it % nbuf], (uint32_t)((it / nbuf) & 1), kWaitLimitNs);
+}
+
+// Write chunk j back from shared memory (one thread) and release its slot once read.
+template <typename T2>
+__device__ __forceinline__ void store_chunk(T2 *state, int c, int64_t j, const T2 *buf, uint64_t *empty_slot,
+                                            const GatherArgs &ga, const CUtensorMap *tmap) {
+    const int chunk_amps = 1 << c;
+    const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
+    const unsigned char *srcs = reinterpret_cast<const unsigned char *>(buf);
+    if (ga.rank > 0) {
+        for (int t = 0; t < (1 << ga.nloop); ++t) {
+            int coord[5];
+            gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
+            ptx::tensor_s2g(tmap, coord, ga.rank, srcs + (size_t)t * ga.box_amps * sizeof(T2));
+        }
+    } else {
+        unsigned char *dstg = reinterpret_cast<unsigned char *>(state + j * chunk_amps);
+        for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+            const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
+            ptx::bulk_s2g(dstg + o, srcs + o, b);
+        }
+    }
+    ptx::bulk_commit();
+    ptx::bulk_wait_read<0>();
+    ptx::mbar_arrive(empty_slot);
 }
 
 constexpr int CG = 2;  // consumer groups per CTA
@@ -255,38 +343,8 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
 
     if (threadIdx.x < 32) {
         // ------------------------------------------------------------ producer
-        if (threadIdx.x != 0) return;
-        int64_t issued = 0;
-        for (int64_t it = 0; it < count; ++it) {
-            const int s = (int)(it % nbuf);
-            if (it >= nbuf) {
-                if (!ptx::mbar_wait(&empty[s], (uint32_t)((it / nbuf - 1) & 1), kWaitLimitNs) || *abort_flag) {
-                    atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                    break;
-                }
-            }
-            const int64_t j = blockIdx.x + it * gridDim.x;
-            unsigned char *dst = reinterpret_cast<unsigned char *>(bufs + (size_t)s * chunk_amps);
-            ptx::mbar_arrive_expect_tx(&full[s], chunk_bytes);
-            if (ga.rank > 0) {
-                for (int t = 0; t < (1 << ga.nloop); ++t) {
-                    int coord[5];
-                    gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
-                    ptx::tensor_g2s(dst + (size_t)t * ga.box_amps * sizeof(T2), &tmap, coord, ga.rank, &full[s]);
-                }
-            } else {
-                const unsigned char *src = reinterpret_cast<const unsigned char *>(state + j * chunk_amps);
-                for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
-                    const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
-                    ptx::bulk_g2s(dst + o, src + o, b, &full[s]);
-                }
-            }
-            ++issued;
-        }
-        // do not leave while copies into this CTA's shared memory are still in flight
-        for (int64_t it = issued > nbuf ? issued - nbuf : 0; it < issued; ++it)
-            (void)ptx::mbar_wait(&full[it % nbuf], (uint32_t)((it / nbuf) & 1), kWaitLimitNs);
+        if (threadIdx.x == 0)
+            produce_chunks<T2>(state, c, count, nbuf, bufs, full, empty, abort_flag, err, ga, &tmap);
         return;
     }
 
@@ -329,26 +387,8 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
             break;
         }
         if (nseg == 0) ptx::fence_proxy_async_smem();
-        if (ctid == 0) {
-            const unsigned char *srcs = reinterpret_cast<const unsigned char *>(buf);
-            if (ga.rank > 0) {
-                for (int t = 0; t < (1 << ga.nloop); ++t) {
-                    int coord[5];
-                    gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
-                    ptx::tensor_s2g(&tmap, coord, ga.rank, srcs + (size_t)t * ga.box_amps * sizeof(T2));
-                }
-            } else {
-                unsigned char *dstg = reinterpret_cast<unsigned char *>(state + j * chunk_amps);
-                for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
-                    const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
-                    ptx::bulk_s2g(dstg + o, srcs + o, b);
-                }
-            }
-            ptx::bulk_commit();
-            // release the buffer to the producer once the write-back has read it
-            ptx::bulk_wait_read<0>();
-            ptx::mbar_arrive(&empty[s]);
-        }
+        // release the buffer to the producer once the write-back has read it
+        if (ctid == 0) store_chunk<T2>(state, c, j, buf, &empty[s], ga, &tmap);
     }
     if (ctid == 0) ptx::bulk_wait<0>();
     if constexpr (TC) {

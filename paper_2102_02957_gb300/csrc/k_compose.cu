@@ -82,6 +82,25 @@ __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate
             }
         }
     }
+    // unitarity of the fused matrix (in FP64): max |(U^H U - I)_ij| over all i, j
+    __shared__ double ur[16][17], ui[16][17];
+    __shared__ unsigned long long dev_bits;
+    if (j == 0) dev_bits = 0;
+    for (int r = 0; r < 16; ++r) { ur[r][j] = vr[r]; ui[r][j] = vi[r]; }
+    __syncthreads();
+    double worst = 0.0;
+    for (int i = 0; i < 16; ++i) {
+        double gr = 0.0, gi = 0.0;  // <U e_i, U e_j>
+        for (int r = 0; r < 16; ++r) {
+            gr += ur[r][i] * ur[r][j] + ui[r][i] * ui[r][j];
+            gi += ur[r][i] * ui[r][j] - ui[r][i] * ur[r][j];
+        }
+        worst = fmax(worst, fabs(gr - (i == j ? 1.0 : 0.0)) + fabs(gi));
+    }
+    atomicMax(&dev_bits, (unsigned long long)__double_as_longlong(worst));  // non-negative: order as integers
+    __syncthreads();
+    if (j == 0)
+        *reinterpret_cast<int *>(prog + sg.b_off + 8192) = __longlong_as_double((long long)dev_bits) <= 1e-10 ? 1 : 0;
     // column j of U is (vr, vi); write B entries with input index c = j
     unsigned char *bhi = prog + sg.b_off, *blo = bhi + 4096;
     for (int r = 0; r < 16; ++r) {

@@ -170,7 +170,9 @@ struct ComposeSeg {
     uint32_t b_off;   // byte offset of the group's B_hi (B_lo follows at +4096) in the program
     int32_t pad;
 };
-constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
+// B_hi + B_lo of one register group (2 x 32 x 32 TF32), then a 16-byte word: its first int is
+// 1 when the fused FP64 matrix is unitary to 1e-10 (max |U^H U - I|), else 0.
+constexpr int TC_B_BYTES = 8192 + 16;
 
 // Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
 // k < low (the contiguous low run of the chunk) and high[k - low] above it; the chunk index

@@ -1,0 +1,105 @@
+"""Parity at the benchmark's full sizes, in the launch configurations the benchmark times.
+
+* quantum volume, n = 30, depth 30, complex64 (8 GiB), chunk 13, gathered chunks with 4 pinned
+  bits, on the tensor-core and on the SIMT register-group paths: every amplitude against the
+  oracle's complex128 simulation (16 GiB on the host; about two minutes of host cores);
+* the same circuit followed by its inverse returns |0..0> (tensor-core path);
+* QFT of a seeded basis state, n = 28, complex128 (4 GiB), chunk 12 with the paper's chunk_swap
+  layout and the final reordering: every amplitude against the closed form;
+* random-layer circuit, n = 28, depth 40, complex128: the cache-blocked path (chunk 12) against
+  the per-gate path, every amplitude, and the mirror circuit back to |0..0>.
+
+Tolerances as everywhere: complex64 1e-5 max-abs and 1 - F <= 1e-8; complex128 1e-12."""
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from oracle import sim
+
+from gpu_util import assert_close, compare, host_ram_bytes
+
+pytestmark = pytest.mark.gpu
+
+GIB = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2102_02957_gb300 as m
+    return m
+
+
+def _need_host(gib):
+    if host_ram_bytes() < gib * GIB:
+        pytest.skip(f"needs {gib} GiB of host memory")
+
+
+@pytest.fixture(scope="module")
+def qv30_oracle():
+    _need_host(48)
+    return sim.simulate(30, cg.build("qv30"))
+
+
+def _run(sv, n, desc, dtype, basis=0, **plan_opts):
+    g = sv.make_gates(desc)
+    with sv.StateVector(n, dtype) as st:
+        st.init_basis(basis)
+        st.apply(g, sv.Plan(n, g, **plan_opts) if plan_opts else None)
+        st.synchronize()
+        return st.get_state()
+
+
+@pytest.mark.parametrize("use_tc", [1, 0])
+def test_quantum_volume_30_bench_config_vs_oracle(sv, qv30_oracle, use_tc):
+    w = cg.WORKLOADS["qv30"]
+    got = _run(sv, 30, cg.build("qv30"), "c64", chunk_bits=w["c"], gather_pinned=4, use_tc=use_tc, seg_bits=4)
+    mx, inf = assert_close(got, qv30_oracle, "c64")
+    print(f"qv30 use_tc={use_tc}: max-abs {mx:.3e}, 1-F {inf:.3e}")
+
+
+def test_quantum_volume_30_mirror_returns_to_zero(sv):
+    _need_host(24)
+    desc = cg.mirror(cg.build("qv30"))
+    got = _run(sv, 30, desc, "c64", chunk_bits=13, gather_pinned=4, use_tc=1)
+    err = np.abs(got[1:]).max()
+    assert abs(complex(got[0]) - 1.0) <= 1e-5 and err <= 1e-5, (complex(got[0]), err)
+
+
+def test_qft_28_closed_form_paper_layout(sv):
+    _need_host(24)
+    n = 28
+    x = cg.basis_index(n, 2)
+    got = _run(sv, n, cg.qft(n), "c128", basis=x, chunk_bits=12)
+    worst = 0.0
+    piece = 1 << 24
+    for s in range(0, 1 << n, piece):
+        y = np.arange(s, s + piece, dtype=np.int64)
+        ref = np.exp(2j * np.pi * ((x * y) % (1 << n)) / (1 << n)) / 2 ** (n / 2)
+        worst = max(worst, float(np.abs(got[s:s + piece] - ref).max()))
+    assert worst <= 1e-12, worst
+
+
+def test_random_layers_28_blocked_vs_per_gate(sv):
+    _need_host(24)
+    n = 28
+    desc = cg.build("rl28")
+    blocked = _run(sv, n, desc, "c128", chunk_bits=12)
+    per_gate = _run(sv, n, desc, "c128")
+    mx, inf = compare(blocked, per_gate)
+    assert mx <= 1e-12 and inf <= 1e-12, (mx, inf)
+    del per_gate
+    norm = sum(float(np.vdot(blocked[s:s + (1 << 24)], blocked[s:s + (1 << 24)]).real)
+               for s in range(0, 1 << n, 1 << 24))
+    assert abs(norm - 1.0) <= 1e-12
+
+
+def test_random_layers_28_mirror_returns_to_zero(sv):
+    _need_host(12)
+    n = 28
+    got = _run(sv, n, cg.mirror(cg.build("rl28")), "c128", chunk_bits=12)
+    assert abs(got[0] - 1.0) <= 1e-12 and np.abs(got[1:]).max() <= 1e-12
