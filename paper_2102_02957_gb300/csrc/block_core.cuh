@@ -65,11 +65,6 @@ __device__ __forceinline__ int lds_s16(uint32_t a) {
     asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
-__device__ __forceinline__ int lds_s32(uint32_t a) {
-    int v;
-    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
 __device__ __forceinline__ void ldc_i4(uint32_t a, int &x, int &y, int &z, int &w) {
     asm("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
 }
@@ -276,6 +271,16 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
     const int g0 = lds_s16(seg + 32), g1 = lds_s16(seg + 34);
     const int G = 1 << (c - R);
 
+    // byte steps between a group's amplitudes in Gray-code order: both the natural and the
+    // swizzled address are linear over GF(2) in the group index, so each next amplitude is one
+    // XOR away (load side and store side may use different layouts)
+    uint32_t ld_step[R], st_step[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        ld_step[j] = (uint32_t)((flags & 1) ? po[j] : pf[j]) << SH;
+        st_step[j] = (uint32_t)((flags & 2) ? po[j] : pf[j]) << SH;
+    }
+
     for (int gb = ctid; gb < G; gb += NC * KU) {
         T re[KU][NA], im[KU][NA];
         int base[KU], sbase[KU];
@@ -289,14 +294,14 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
             base[u] = bs;
             sbase[u] = bs ^ fb;
             if (gb + u * NC < G) {
+                // the offset stays below the chunk size, so it is walked by XOR and the buffer
+                // base (not aligned to the chunk size) added after
+                uint32_t off = (uint32_t)((flags & 1) ? base[u] : sbase[u]) << SH;
 #pragma unroll
                 for (int b = 0; b < NA; ++b) {
-                    int o = 0, f = 0;
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
-                    const int a = (flags & 1) ? (base[u] | o) : (sbase[u] ^ f);
-                    SM<T>::ld(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                    if (b) off ^= ld_step[__ffs(b) - 1];
+                    const int gidx = b ^ (b >> 1);
+                    SM<T>::ld(buf + off, re[u][gidx], im[u][gidx]);
                 }
             }
         }
@@ -310,14 +315,12 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
             if (gb + u * NC < G) {
+                uint32_t off = (uint32_t)((flags & 2) ? base[u] : sbase[u]) << SH;
 #pragma unroll
                 for (int b = 0; b < NA; ++b) {
-                    int o = 0, f = 0;
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        if (b & (1 << j)) { o |= po[j]; f ^= pf[j]; }
-                    const int a = (flags & 2) ? (base[u] | o) : (sbase[u] ^ f);
-                    SM<T>::st(buf + ((uint32_t)a << SH), re[u][b], im[u][b]);
+                    if (b) off ^= st_step[__ffs(b) - 1];
+                    const int gidx = b ^ (b >> 1);
+                    SM<T>::st(buf + off, re[u][gidx], im[u][gidx]);
                 }
             }
         }

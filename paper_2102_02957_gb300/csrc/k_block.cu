@@ -104,15 +104,9 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
     // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
     bool failed = false;
-    // The tensor cores' FP32 accumulation truncates, which shrinks every result by a few units
-    // in the last place -- a bias that compounds over hundreds of register groups.  For a
-    // unitary group the exact row keeps its norm, so each row of D is rescaled to the norm of its
-    // input row (the radial part of the error is removed; what remains is unbiased rounding).
-    const bool unitary = lds_s32(bhi + 8192) != 0;
-    auto stage = [&](int t, int k, int &base, int &sbase, float &nrm) -> bool {
+    auto stage = [&](int t, int k, int &base, int &sbase) -> bool {
         row_base(t, base, sbase);
         uint32_t ahi[32], alo[32];
-        nrm = 0.f;
         // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
         // buffer base is only 1 KiB aligned, so it is added after the XOR walk, never XORed
         uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
@@ -126,7 +120,6 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
             ahi[2 * gidx + 1] = __float_as_uint(xi);
             alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u));
             alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u));
-            nrm = fmaf(xr, xr, fmaf(xi, xi, nrm));
         }
         const uint32_t col = tcol + (uint32_t)k * 96;
         ptx::tmem_st32(col + lane_off, ahi);
@@ -154,7 +147,7 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     };
     // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
     // (after an expired wait the tile is garbage; the group stops at its next barrier)
-    auto finish = [&](int k, int base, int sbase, float nrm) {
+    auto finish = [&](int k, int base, int sbase) {
         if (!ptx::mbar_wait(&mbar[k], phase[k], kWaitLimitNs)) {
             failed = true;
             *abort_flag = 1;
@@ -164,17 +157,6 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         uint32_t y[32];
         ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
         ptx::tmem_wait_ld();
-        if (unitary) {
-            // y <- y (1 + d), d = sqrt(nrm / ny) - 1 ~ (nrm - ny) / (2 ny): applied as a small
-            // correction, since a scale factor rounded to FP32 next to 1 would itself be off by a
-            // nearly constant half unit in the last place for every row
-            float ny = 0.f;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) ny = fmaf(__uint_as_float(y[q]), __uint_as_float(y[q]), ny);
-            const float d = ny > 0.f ? 0.5f * (nrm - ny) / ny : 0.f;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) y[q] = __float_as_uint(fmaf(__uint_as_float(y[q]), d, __uint_as_float(y[q])));
-        }
         uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
 #pragma unroll
         for (int b = 0; b < NA; ++b) {
@@ -185,18 +167,15 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     };
     // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
     int pb, ps;
-    float pn;
-    if (!stage(0, 0, pb, ps, pn)) return false;
+    if (!stage(0, 0, pb, ps)) return false;
     for (int t = 1; t < T; ++t) {
         int nb, ns;
-        float nn;
-        if (!stage(t, t & 1, nb, ns, nn)) return false;
-        finish((t - 1) & 1, pb, ps, pn);
+        if (!stage(t, t & 1, nb, ns)) return false;
+        finish((t - 1) & 1, pb, ps);
         pb = nb;
         ps = ns;
-        pn = nn;
     }
-    finish((T - 1) & 1, pb, ps, pn);
+    finish((T - 1) & 1, pb, ps);
     return !ptx::named_bar_or(bar_id, NC, failed);  // the group leaves together
 }
 

@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t b_offset(int k, int n) {
 
 // One CTA per register group, thread j composes column j of U (U e_j through the group's gates).
 __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate<double> *__restrict__ gates,
-                              unsigned char *__restrict__ prog) {
+                              unsigned char *__restrict__ prog, int *__restrict__ all_unitary) {
     const ComposeSeg sg = segs[blockIdx.x];
     const int j = threadIdx.x;  // 0..15
     double vr[16], vi[16];
@@ -99,8 +99,7 @@ __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate
     }
     atomicMax(&dev_bits, (unsigned long long)__double_as_longlong(worst));  // non-negative: order as integers
     __syncthreads();
-    if (j == 0)
-        *reinterpret_cast<int *>(prog + sg.b_off + 8192) = __longlong_as_double((long long)dev_bits) <= 1e-10 ? 1 : 0;
+    if (j == 0 && !(__longlong_as_double((long long)dev_bits) <= 1e-10)) atomicAnd(all_unitary, 0);
     // column j of U is (vr, vi); write B entries with input index c = j
     unsigned char *bhi = prog + sg.b_off, *blo = bhi + 4096;
     for (int r = 0; r < 16; ++r) {
@@ -120,10 +119,11 @@ __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate
 
 }  // namespace
 
-void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st) {
+void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary,
+                    cudaStream_t st) {
     if (nseg <= 0) return;
     k_compose_f64<<<nseg, 16, 0, st>>>((const ComposeSeg *)dev_segs, (const DevGate<double> *)dev_gates,
-                                       (unsigned char *)dev_prog);
+                                       (unsigned char *)dev_prog, all_unitary);
     check_cuda(cudaGetLastError(), "compose kernel launch");
 }
 

@@ -40,16 +40,71 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;
 }
 
-// Each CTA sums a contiguous range of 2^n / gridDim.x amplitudes (the partials are added on
-// the host in CTA order, so the result does not depend on scheduling).
-template <typename T2>
-__global__ void __launch_bounds__(kThreads) k_partial_norm(const T2 *__restrict__ a, int64_t len, double *partials) {
+// Each CTA sums a contiguous range of the state (the partials are added in CTA order, so the
+// result does not depend on scheduling).  complex64: threads read 16-byte vectors (two
+// amplitudes); squares are summed in FP32 over runs of 8 vectors per thread (16 terms, all
+// non-negative) and the runs accumulated in FP64 -- FP64 arithmetic on every element would
+// make this pass FP64-bound instead of HBM-bound on GB300.  complex128: FP64 throughout.
+__global__ void __launch_bounds__(kThreads) k_partial_norm_c64(const float4 *__restrict__ v, int64_t nv,
+                                                               double *partials) {
+    const int64_t per = (nv + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < nv ? lo + per : nv;
+    double s = 0;
+    for (int64_t base = lo + threadIdx.x; base < hi; base += 8 * kThreads) {
+        float f = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t i = base + (int64_t)k * kThreads;
+            if (i < hi) {
+                const float4 q = v[i];
+                f = fmaf(q.x, q.x, fmaf(q.y, q.y, fmaf(q.z, q.z, fmaf(q.w, q.w, f))));
+            }
+        }
+        s += (double)f;
+    }
+    s = block_sum<kThreads>(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_partial_norm_c128(const double2 *__restrict__ a, int64_t len,
+                                                                double *partials) {
     const int64_t per = (len + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < len ? lo + per : len;
     double s = 0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) s += p2(a[i]);
     s = block_sum<kThreads>(s);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Norm restoration after a tensor-core circuit: d = sqrt(n_in / n_out) - 1 from the two sets of
+// norm partials (input at part[0, nb), output at part[nb, 2 nb)), applied only when every fused
+// group was unitary (*flag != 0).
+__global__ void k_renorm_factor(const double *__restrict__ part, int nb, const int *__restrict__ flag,
+                                float *__restrict__ out) {
+    double nin = 0, nout = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        nin += part[b];
+        nout += part[nb + b];
+    }
+    nin = block_sum<kThreads>(nin);
+    nout = block_sum<kThreads>(nout);
+    if (threadIdx.x == 0) out[0] = (*flag != 0 && nout > 0) ? (float)(sqrt(nin / nout) - 1.0) : 0.f;
+}
+
+// a <- a (1 + d), applied as a small correction so that the factor's FP32 rounding next to 1
+// does not become the error.
+template <typename V>
+__global__ void __launch_bounds__(kThreads) k_renorm_apply(V *__restrict__ v, int64_t nv, const float *__restrict__ dp) {
+    const float d = *dp;
+    if (d == 0.f) return;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < nv; i += (int64_t)gridDim.x * kThreads) {
+        V q = v[i];
+        q.x = fmaf(q.x, d, q.x);
+        q.y = fmaf(q.y, d, q.y);
+        q.z = fmaf(q.z, d, q.z);
+        q.w = fmaf(q.w, d, q.w);
+        v[i] = q;
+    }
 }
 
 // sum_j conj(a_{j^x}) a_j (-1)^{popc(j & z)}; the phase i^{popc(x&z)} is applied on the host.
@@ -128,11 +183,24 @@ void launch_probs(int dtype, const void *state, int n, double *out, int64_t firs
 
 void launch_partial_norm(int dtype, const void *state, int n, double *partials, int nblocks, cudaStream_t st) {
     const int64_t len = int64_t(1) << n;
-    if (dtype == SV_C64)
-        k_partial_norm<float2><<<nblocks, kThreads, 0, st>>>((const float2 *)state, len, partials);
+    if (dtype == SV_C64)  // n >= 1: an even number of amplitudes
+        k_partial_norm_c64<<<nblocks, kThreads, 0, st>>>((const float4 *)state, len / 2, partials);
     else
-        k_partial_norm<double2><<<nblocks, kThreads, 0, st>>>((const double2 *)state, len, partials);
+        k_partial_norm_c128<<<nblocks, kThreads, 0, st>>>((const double2 *)state, len, partials);
     check_cuda(cudaGetLastError(), "norm kernel launch");
+}
+
+void launch_renorm(int dtype, void *state, int n, const double *partials, int nblocks, const int *flag, float *d,
+                   cudaStream_t st) {
+    k_renorm_factor<<<1, kThreads, 0, st>>>(partials, nblocks, flag, d);
+    check_cuda(cudaGetLastError(), "renorm factor launch");
+    const int64_t nv = (int64_t(1) << n) / (dtype == SV_C64 ? 2 : 1);
+    const int grid = (int)std::min<int64_t>((nv + kThreads - 1) / kThreads, (int64_t)num_sms() * 8);
+    if (dtype == SV_C64)
+        k_renorm_apply<float4><<<grid, kThreads, 0, st>>>((float4 *)state, nv, d);
+    else
+        fail(SV_ERR_UNSUPPORTED, "norm restoration is for complex64 tensor-core circuits");
+    check_cuda(cudaGetLastError(), "renorm launch");
 }
 
 void launch_partial_expval(int dtype, const void *state, int n, uint64_t x, uint64_t z, double *partials, int nblocks,

@@ -170,9 +170,7 @@ struct ComposeSeg {
     uint32_t b_off;   // byte offset of the group's B_hi (B_lo follows at +4096) in the program
     int32_t pad;
 };
-// B_hi + B_lo of one register group (2 x 32 x 32 TF32), then a 16-byte word: its first int is
-// 1 when the fused FP64 matrix is unitary to 1e-10 (max |U^H U - I|), else 0.
-constexpr int TC_B_BYTES = 8192 + 16;
+constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
 
 // Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
 // k < low (the contiguous low run of the chunk) and high[k - low] above it; the chunk index
@@ -192,7 +190,10 @@ constexpr int kBatchMaxProgBytes = 24 * 1024;
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
                   int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int *dev_err,
                   cudaStream_t st);
-void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, cudaStream_t st);
+// Fuse the register groups in FP64; *all_unitary (1 on entry) is cleared when a fused matrix
+// is not unitary to 1e-10 (max |U^H U - I|).
+void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary,
+                    cudaStream_t st);
 
 // cost-model network kernels (k_mlp.cu)
 int mlp_param_count();
@@ -233,6 +234,10 @@ void launch_probs(int dtype, const void *state, int n, double *out, int64_t firs
                   cudaStream_t st);
 void launch_partial_norm(int dtype, const void *state, int n, double *partials, int nblocks,
                          cudaStream_t st);
+// state <- state * sqrt(n_in / n_out) (complex64) when *flag != 0; partials: n_in's nblocks
+// partial sums, then n_out's; d: one float of device scratch.
+void launch_renorm(int dtype, void *state, int n, const double *partials, int nblocks, const int *flag, float *d,
+                   cudaStream_t st);
 void launch_partial_expval(int dtype, const void *state, int n, uint64_t x, uint64_t z,
                            double *partials, int nblocks, cudaStream_t st);
 void launch_block_sums(int dtype, const void *state, int n, int sum_bits, double *sums, cudaStream_t st);
