@@ -429,6 +429,28 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ cost model
+def _train_cost_model(sv, st, w, plan_opts):
+    """Collect section timings of two circuits of the workload's family (same size, other seeds)
+    under the paper's rule and under random candidate choices, and train the network on them."""
+    import circuitgen as cg
+    t0 = time.perf_counter()
+    n = w["n"]
+    fam = {"quantum_volume": lambda s: cg.quantum_volume(n, w.get("depth", 30), s),
+           "random_layers": lambda s: cg.random_layers(n, w.get("depth", 30), s),
+           "qft": lambda s: cg.qft(n)}[w["kind"]]
+    cm = sv.CostModel(17)
+    opts = [dict(plan_opts)]
+    for k, seed in enumerate((1001, 1002)):
+        g = sv.make_gates(fam(seed))
+        cm.collect(st, g, opts, policy_seed=0)
+        cm.collect(st, g, opts, policy_seed=5000 + k)
+    mse = cm.train(epochs=400, batch=64, lr=2e-3, seed=3)
+    info = {"samples": cm.num_samples(), "train_mse_log_us": mse, "seconds": time.perf_counter() - t0,
+            "trained_on": f"{w['kind']} n={n} seeds 1001-1002, rule and random candidate choices"}
+    return cm, info
+
+
 # ------------------------------------------------------------------ main GPU benchmark
 def run_ours(args):
     import numpy as np
@@ -451,12 +473,18 @@ def run_ours(args):
     plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=args.gather_pinned, use_tc=int(args.tc))
     stream = torch.cuda.Stream()
     st = sv.StateVector(n, "c64", stream=stream)
-    st.set_profiling(True)
     sweep_bytes = 2.0 * (1 << n) * 8
 
-    def step():
+    # learned cost model (steered planner): trained before the timed region on section timings of
+    # circuits of the same family and size with other seeds
+    model, model_info = None, None
+    if args.planner == "steered":
+        model, model_info = _train_cost_model(sv, st, w, plan_opts)
+    st.set_profiling(True)
+
+    def step(use_model=True):
         gates = sv.make_gates(desc)
-        plan = sv.Plan(n, gates, **plan_opts)
+        plan = sv.Plan(n, gates, model=model if use_model else None, **plan_opts)
         st.init_basis(0)
         st.apply(gates, plan)
         nrm = st.norm2()
@@ -514,6 +542,25 @@ def run_ours(args):
                 "k_permute": {"launches_per_step": info.n_swap_rounds + info.n_unpermute_rounds, "ms": perm_ms,
                               "GBs": perm_gbs, "share": ms_perm / (ms_block + ms_perm)}}
 
+    # the paper's rule-based planner on the same workload, for comparison with the steered one
+    rule = None
+    if model is not None:
+        rule_info = None
+        for _ in range(1):
+            step(use_model=False)
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        k_rule = max(1, min(2, args.steps))
+        r0.record(stream)
+        for _ in range(k_rule):
+            _, rplan = step(use_model=False)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rule_info = rplan.info()
+        rule = {"ms_per_step": r0.elapsed_time(r1) / k_rule, "sections": rule_info.n_blocks,
+                "gates_per_s": G / (r0.elapsed_time(r1) / k_rule / 1000.0)}
+
     # plain per-gate GPU path on the same workload (the paper's baseline)
     per_gate = None
     pg_ms = float("nan")
@@ -569,6 +616,7 @@ def run_ours(args):
             "effective_hbm_GBs": eff_gbs, "effective_hbm_frac": eff_gbs / peak,
             "sweeps_per_step": {"blocks": info.n_blocks, "swap_rounds": info.n_swap_rounds,
                                 "reorder_rounds": info.n_unpermute_rounds},
+            "planner": args.planner, "cost_model": model_info, "rule_planner": rule,
             "per_gate": per_gate, "speedup_vs_per_gate": (pg_ms / ms_step) if per_gate else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": launches, "norm": norm_last,
@@ -593,6 +641,8 @@ def main():
     ap.add_argument("--tc", type=int, default=1, help="1: fused register groups on the tensor cores (3xTF32)")
     ap.add_argument("--gather-pinned", type=int, default=4,
                     help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
+    ap.add_argument("--planner", default="steered", choices=["rule", "steered"],
+                    help="steered: the learned cost model picks each section's chunk (trained before timing)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()
