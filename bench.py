@@ -235,16 +235,31 @@ def args_workload_name(w):
     return f"{kinds[w['kind']]} n={w['n']}{depth}, {len(w['desc'])} gates, complex64, chunk c={w['c']}"
 
 
+# sources a kernel's binary depends on (the kernel file first)
+_KERNEL_SOURCES = {
+    "k_block.cu": ["k_block.cu", "block_core.cuh", "ptx.cuh", "sv_internal.h"],
+    "k_batch.cu": ["k_batch.cu", "block_core.cuh", "ptx.cuh", "sv_internal.h"],
+}
+
+
+def kernel_source_sha(kernel_src: str) -> str:
+    csrc = os.path.join(ROOT, os.path.dirname(kernel_src))
+    h = hashlib.sha256()
+    for name in _KERNEL_SOURCES.get(os.path.basename(kernel_src), [os.path.basename(kernel_src)]):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_for(kernel_src: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    source of the kernel; else None."""
+    sources of the kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    with open(os.path.join(ROOT, kernel_src), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    sha = kernel_source_sha(kernel_src)
     e = d.get(workload, {}).get(os.path.basename(kernel_src))
     if not e or e.get("source_sha") != sha:
         return None
@@ -306,6 +321,37 @@ def cpu_oracle_batch_rate(ns, descs, budget_s: float):
     return total / est, sim.num_threads(), sample
 
 
+# Algorithmic FP32 FMAs per amplitude of each gate kind (complex64): a dense 2x2 complex matrix
+# costs 4 complex multiply-adds per amplitude pair = 8 real FMAs per amplitude, a dense 4x4 16,
+# a diagonal one complex multiply = 4, a permutation (X, CX, SWAP) none.
+_FMA_PER_AMP = {"u3": 8, "h": 8, "y": 8, "ry": 8, "unitary1": 8, "x": 0, "z": 4, "rz": 4, "cz": 4, "cp": 4,
+                "cx": 0, "swap": 0}
+
+
+def _algorithmic_fma(ns, descs):
+    tot = 0.0
+    for n, d in zip(ns, descs):
+        per = 0
+        for kind, qubits, _ in d:
+            if kind == "unitary":
+                per += 8 if len(qubits) == 1 else 16
+            else:
+                per += _FMA_PER_AMP[kind]
+        tot += float(per) * float(1 << n)
+    return tot
+
+
+def _fp32_peak_tflops():
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def run_batch(args):
     import numpy as np
     import torch
@@ -358,10 +404,17 @@ def run_batch(args):
     value = world * G * args.steps / (elapsed_ms / 1000.0)
     peak, peak_kind = _peaks()
     achieved = nbytes / (ms_step / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+    # the batch is bound by FP32 arithmetic, not HBM: its roofline is the FMA pipes
+    flops = 2.0 * _algorithmic_fma(ns, descs)
+    alu_peak = _fp32_peak_tflops()
+    achieved_tf = flops / (ms_step / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_batch", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak,
+                "peak_source": "derived: SMs x 128 FP32 FMA lanes x 2 flops x max SM clock (MEASURED_PEAKS.json)",
                 "traffic": _traffic_for("paper_2102_02957_gb300/csrc/k_batch.cu", args.workload),
-                "algorithmic_bytes_per_launch": nbytes, "launch_ms": ms_step}
+                "algorithmic_flops_per_launch": flops, "launch_ms": ms_step,
+                "hbm": {"algorithmic_bytes_per_launch": nbytes, "achieved_GBs": achieved, "peak_GBs": peak,
+                        "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"}}
     norms = [s.norm2() for s in states[:: max(1, len(states) // 16)]]
 
     # the same circuits one state after another on the single-state blocked path
