@@ -110,12 +110,19 @@ def _dist():
 
 
 class _Barrier:
-    def __init__(self, world, device):
+    """Rank synchronisation for replica runs: a barrier and a max over ranks (timings only; the
+    simulation itself exchanges nothing).  NCCL on GPUs; gloo for host-only use."""
+
+    def __init__(self, world, device, backend: str = "nccl"):
         self.world = world
         self.pg = None
+        self.backend = backend
         if world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl", device_id=device)
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group(backend)
             self.pg = dist
 
     def barrier(self):
@@ -126,7 +133,7 @@ class _Barrier:
         if not self.pg:
             return v
         import torch
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self.backend == "nccl" else "cpu")
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 

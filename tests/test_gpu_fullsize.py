@@ -103,3 +103,29 @@ def test_random_layers_28_mirror_returns_to_zero(sv):
     n = 28
     got = _run(sv, n, cg.mirror(cg.build("rl28")), "c128", chunk_bits=12)
     assert abs(got[0] - 1.0) <= 1e-12 and np.abs(got[1:]).max() <= 1e-12
+
+
+def test_random_layers_33_complex128_mirror(sv):
+    """Config 5's largest state: n = 33 complex128 (128 GiB of HBM), random layers depth 32 and
+    its inverse on the cache-blocked path (chunk 12, the paper's layout) must return |0..0>;
+    checked on the device through the FP64 probability readout (no 128 GiB host copy)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200 * GIB:
+        pytest.skip("needs 200 GiB of free device memory")
+    n = 33
+    desc = cg.mirror(cg.random_layers(n, 32, 7))
+    g = sv.make_gates(desc)
+    with sv.StateVector(n, "c128") as st:
+        st.init_basis(0)
+        st.apply(g, sv.Plan(n, g, chunk_bits=12))
+        st.synchronize()
+        p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        st.probabilities(p)
+        torch.cuda.synchronize()
+        p0 = float(p[0])
+        p[0] = 0.0
+        rest = float(p.max())
+        total = float(p.sum()) + p0
+        del p
+    assert abs(p0 - 1.0) <= 1e-11 and rest <= 1e-20 and abs(total - 1.0) <= 1e-11, (p0, rest, total)
