@@ -84,7 +84,11 @@ typedef struct sv_options {
                                gathered chunks -- a chunk is the low p bits plus c-p chosen bits,
                                fetched in place (no chunk_swap passes, no data reordering); the
                                transpiler's choice rule starts from the p pinned bits.  default 0 */
-    int32_t reserved[8];
+    int32_t diag_outside;   /* 1: diagonal gates (SV_GATE_DIAG with an exactly diagonal matrix) may
+                               join a section while some of their qubits lie outside its chunk: those
+                               qubits are constant over a chunk, so the gate acts there as a diagonal
+                               on its chunk qubits (or a phase).  Ignored with use_tc.  default 0 */
+    int32_t reserved[7];
 } sv_options;
 
 void sv_options_default(sv_options *opts);

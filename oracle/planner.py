@@ -32,6 +32,11 @@ physical bit q holds logical qubit q (Sec. IV.C: "reorder qubits for the output"
 for each cycle x0 -> x1 -> ... (x0 its smallest bit, x_{i+1} = destination of x_i) the first
 round exchanges x_i <-> x_{L-i} and the second x_i <-> x_{L+1-i} (indices mod L).
 
+Diagonal gates (``diag_outside``): a gate whose matrix is diagonal (Z, RZ, CP, CZ) may join a
+section while some of its qubits are outside the chunk, because those qubits are constant over a
+chunk -- the gate acts there as a diagonal on its chunk qubits, or as a phase.  It is taken when
+its chunk qubits are not in QB_BLOCKED and no earlier deferred gate touches its outside qubits.
+
 Gathered chunks (``pinned > 0``): the same loop without data movement.  A chunk is any set of c
 bits that contains the low ``pinned`` bits; the section gathers it from HBM instead of having
 chunk_swap rounds make it contiguous.  QB_CHUNK starts as the pinned qubits and is filled by the
@@ -103,7 +108,11 @@ def _canonical_qubits(kind, qubits):
     return tuple(sorted(qubits))
 
 
-def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True, pinned: int = 0) -> Plan:
+DIAGONAL_KINDS = ("z", "rz", "cp", "cz")
+
+
+def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True, pinned: int = 0,
+                  diag_outside: bool = False) -> Plan:
     if not (1 <= n <= 62):
         raise ValueError("n out of range")
     if c < 1:
@@ -120,6 +129,7 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
     # SWAP gates as relabels: lab[label] = virtual qubit carrying that label.
     lab = list(range(n))
     remaining = []  # (gate index, virtual qubits ascending by label order of description)
+    diag = set()    # gates that may join a section with qubits outside its chunk
     for gi, (kind, qubits, _params) in enumerate(gates):
         for q in qubits:
             if not (0 <= q < n):
@@ -134,6 +144,8 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
         if len(vq) > target:
             raise ValueError(f"gate {gi} is wider than the chunk")
         remaining.append((gi, vq))
+        if diag_outside and kind in DIAGONAL_KINDS:
+            diag.add(gi)
 
     m = list(range(n))  # virtual (logical) qubit -> physical bit
     pinv = list(range(n))  # physical bit -> virtual qubit
@@ -185,16 +197,26 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
             plan.ops.append(("swap", pairs))
 
         # -- scan REMAINING with QB_BLOCKED
+        # diag_outside: a diagonal gate may also take qubits outside the chunk (they are fixed
+        # over a chunk), provided no earlier deferred gate touches those qubits
         blocked = set()
+        out_blocked = set()
         block = []
         nxt = []
         for gi, qs in remaining:
-            if all(q in chosen_set for q in qs) and not any(q in blocked for q in qs):
+            outside = [q for q in qs if q not in chosen_set]
+            if not outside:
+                take = not any(q in blocked for q in qs)
+            else:
+                take = (gi in diag and not any(q in blocked for q in qs if q in chosen_set)
+                        and not any(q in out_blocked for q in outside))
+            if take:
                 block.append((gi, tuple(m[q] for q in qs)))
             else:
                 nxt.append((gi, qs))
                 if any(q in chosen_set for q in qs):
                     blocked.update(qs)
+                out_blocked.update(outside)
         if pinned:
             mask = 0
             for q in chosen:
@@ -240,11 +262,14 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
     return plan
 
 
-def validate(plan: Plan, gates) -> None:
+def validate(plan: Plan, gates, diag_outside: bool = False) -> None:
     """Raise AssertionError unless the plan is a valid cache-blocked schedule of `gates`:
-    every non-SWAP gate is emitted exactly once, every emitted gate's physical bits are < c,
-    every swap round pairs a bit < c with a bit >= c and no bit twice, and the per-qubit gate
-    order of the input is preserved."""
+    every non-SWAP gate is emitted exactly once, every emitted gate's physical bits are in its
+    section's chunk (diagonal gates excepted when `diag_outside`), every swap round pairs a bit
+    < c with a bit >= c and no bit twice, and the per-qubit gate order of the input is
+    preserved."""
+    def exempt(gi):
+        return diag_outside and gates[gi][0] in DIAGONAL_KINDS
     n, c = plan.n, plan.c
     width = min(c, n)
     emitted = []
@@ -267,12 +292,12 @@ def validate(plan: Plan, gates) -> None:
             assert bin(mask).count("1") <= width and mask < (1 << n)
             assert all((mask >> b) & 1 for b in range(plan.pinned)), "pinned bits missing"
             for gi, phys in gl:
-                assert all((mask >> p) & 1 for p in phys), (phys, mask)
+                assert exempt(gi) or all((mask >> p) & 1 for p in phys), (phys, mask)
                 emitted.append(gi)
         else:
             assert len(body) > 0, "empty block"
             for gi, phys in body:
-                assert all(0 <= p < width for p in phys), phys
+                assert all(0 <= p < n for p in phys) and (exempt(gi) or all(p < width for p in phys)), phys
                 emitted.append(gi)
     expect = [gi for gi, g in enumerate(gates) if g[0] != "swap"]
     assert sorted(emitted) == expect, "each gate exactly once"

@@ -254,7 +254,8 @@ class Batch:
             pass
 
 
-_OPT_KEYS = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned")
+_OPT_KEYS = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned",
+             "diag_outside")
 
 
 def batch_tune(states, gate_lists, **base):

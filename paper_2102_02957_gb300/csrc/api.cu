@@ -107,10 +107,13 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::ve
         PlanOp local = op0;
         if (op0.kind == 4) {
             lay = gather_layout(op0.mask, plan->n, 8);
-            for (BlockGate &g : local.gates)
-                for (int j = 0; j < g.nq; ++j) g.phys[j] = lay.local_of[g.phys[j]];
+            local.gates = localize_gates(op0, plan->n, plan->c, &lay);
             width = lay.ce;
+        } else {
+            local.gates = localize_gates(op0, plan->n, plan->c, nullptr);
         }
+        for (const BlockGate &g : local.gates)
+            if (g.ext[0] >= 0 || g.ext[1] >= 0) fail(SV_ERR_PLAN, "tensor-core sections take no gates outside the chunk");
         const std::vector<HostSeg> segs = segment_block(local.gates, width, 4, 8);
         for (size_t p0 = 0; p0 < segs.size(); p0 += kMaxTcSegs) {
             const size_t p1 = std::min(segs.size(), p0 + (size_t)kMaxTcSegs);
@@ -185,15 +188,16 @@ static void build_programs(const sv_plan *plan, const sv_gate *gates, int seg_bi
         BlockProg bp{};
         PlanOp local;
         const PlanOp *opp = &op0;
+        local = op0;
         if (op0.kind == 4) {  // gate bits -> chunk-local bits of the gathered layout
             bp.lay = gather_layout(op0.mask, plan->n, (int)(2 * sizeof(T)));
-            local = op0;
-            for (BlockGate &g : local.gates)
-                for (int j = 0; j < g.nq; ++j) g.phys[j] = bp.lay.local_of[g.phys[j]];
+            local.gates = localize_gates(op0, plan->n, plan->c, &bp.lay);
             width = bp.lay.ce;
-            opp = &local;
             bp.gathered = true;
+        } else {
+            local.gates = localize_gates(op0, plan->n, plan->c, nullptr);
         }
+        opp = &local;
         bp.op_index = (int)(&op0 - plan->ops.data());
         const PlanOp &op = *opp;
         std::vector<HostSeg> segs = segment_block(op.gates, width, seg_bits, (int)(2 * sizeof(T)));

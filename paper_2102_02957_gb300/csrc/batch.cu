@@ -110,6 +110,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
         o.gather_pinned = std::min(4, std::min(o.chunk_bits, h->n) - 2);
         o.reserve = 0;
         o.restore_layout = 1;
+        o.diag_outside = 0;
         for (int64_t i = 0; i < n_gates[s]; ++i)
             if (gates[s][i].flags & SV_GATE_SWAP)
                 fail(SV_ERR_UNSUPPORTED, "sv_batch_create: SWAP relabels are not batched");

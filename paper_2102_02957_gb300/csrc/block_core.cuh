@@ -93,16 +93,35 @@ __device__ __forceinline__ void ap_dense1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
     }
 }
 
+// Diagonal gates.  Complex128 sections are FP64-bound on this GPU, so there an entry of exactly
+// 1 leaves its amplitudes alone (a controlled phase touches a quarter of them; the test is
+// uniform over the warp); complex64 multiplies through, the branch-free form being faster.
+template <typename T>
+__device__ __forceinline__ void scale_amp(T &re, T &im, T dr, T di) {
+    const T xr = re, xi = im;
+    re = fma(dr, xr, -di * xi);
+    im = fma(dr, xi, di * xr);
+}
+
 template <typename T, int NA, int A>
 __device__ __forceinline__ void ap_diag1(T (&r)[NA], T (&i)[NA], uint32_t ma) {
     T d[4];
     load_mat<T, 4>(ma, d);
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int x = 0; x < NA; ++x) {
-        const T dr = (x & (1 << A)) ? d[2] : d[0], di = (x & (1 << A)) ? d[3] : d[1];
-        const T xr = r[x], xi = i[x];
-        r[x] = fma(dr, xr, -di * xi);
-        i[x] = fma(dr, xi, di * xr);
+        for (int l = 0; l < 2; ++l) {
+            const T dr = d[2 * l], di = d[2 * l + 1];
+            if (di == T(0) && dr == T(1)) continue;
+#pragma unroll
+            for (int x = 0; x < NA; ++x)
+                if (((x >> A) & 1) == l) scale_amp(r[x], i[x], dr, di);
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < NA; ++x) {
+            const int l = (x >> A) & 1;
+            scale_amp(r[x], i[x], d[2 * l], d[2 * l + 1]);
+        }
     }
 }
 
@@ -132,13 +151,21 @@ template <typename T, int NA, int A, int B>
 __device__ __forceinline__ void ap_diag2(T (&r)[NA], T (&i)[NA], uint32_t ma) {
     T d[8];
     load_mat<T, 8>(ma, d);
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int x = 0; x < NA; ++x) {
-        const int l = ((x >> A) & 1) | (((x >> B) & 1) << 1);
-        const T dr = d[2 * l], di = d[2 * l + 1];
-        const T xr = r[x], xi = i[x];
-        r[x] = fma(dr, xr, -di * xi);
-        i[x] = fma(dr, xi, di * xr);
+        for (int l = 0; l < 4; ++l) {
+            const T dr = d[2 * l], di = d[2 * l + 1];
+            if (di == T(0) && dr == T(1)) continue;
+#pragma unroll
+            for (int x = 0; x < NA; ++x)
+                if ((((x >> A) & 1) | (((x >> B) & 1) << 1)) == l) scale_amp(r[x], i[x], dr, di);
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < NA; ++x) {
+            const int l = ((x >> A) & 1) | (((x >> B) & 1) << 1);
+            scale_amp(r[x], i[x], d[2 * l], d[2 * l + 1]);
+        }
     }
 }
 
@@ -242,7 +269,7 @@ constexpr int kMaxRest = 8;  // chunk bits above the lanes per register group (c
 // thread handles KU groups at a time so that every gate matrix is read once for all of them.
 template <typename T, int R, int NC, int KU>
 __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t gates, int ctid, const int *swz,
-                                            int c) {
+                                            int c, int64_t origin) {
     constexpr int NA = 1 << R;
     constexpr int SH = sizeof(T) == 4 ? 3 : 4;  // log2 bytes per amplitude
     // descriptor (DevSeg layout: pos[8] lane[5] nrest flags r rest[16] g0 g1)
@@ -309,8 +336,17 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
             const uint32_t ga = gates + (uint32_t)gi * (uint32_t)sizeof(DevGate<T>);
             int op, ra, rb, code;
             ldc_i4(ga, op, ra, rb, code);
+            uint32_t ma = ga + 16;
+            if (op == OP_DIAGX) {
+                // qubits outside the chunk are fixed over it: read them off the chunk's origin
+                const int e0 = rb & 0xFF, e1 = (rb >> 8) & 0xFF;
+                int v = (int)((origin >> e0) & 1);
+                if (e1 != 0xFF) v |= (int)((origin >> e1) & 1) << 1;
+                ma += (uint32_t)(v * 4 * (int)sizeof(T));
+                op = OP_DIAG1;  // a phase is encoded as equal entries on register bit 0
+            }
 #pragma unroll
-            for (int u = 0; u < KU; ++u) apply_gate<T, R>(op, code, ga + 16, re[u], im[u]);
+            for (int u = 0; u < KU; ++u) apply_gate<T, R>(op, code, ma, re[u], im[u]);
         }
 #pragma unroll
         for (int u = 0; u < KU; ++u) {

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NCB) k_batch(const BatchOp *__restrict__ ops, 
             const uint32_t gate_s = seg_s + (uint32_t)((hd.x * sizeof(DevSeg) + 15) & ~size_t(15));
             for (int si = 0; si < hd.x; ++si) {
                 run_segment<float, RB, NCB, 1>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)), gate_s, threadIdx.x,
-                                               c_swz64, ce);
+                                               c_swz64, ce, obase);
                 __syncthreads();
             }
             poff += (uint32_t)hd.z;

@@ -345,6 +345,8 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
         ptx::named_bar_sync(bar_id, NC);
         if (*abort_flag) break;
         T2 *buf = bufs + (size_t)s * chunk_amps;
+        // state index of the chunk's first amplitude (its bits outside the chunk are the chunk's)
+        const int64_t origin = ga.rank > 0 ? gather_origin(ga, j, 0) : j << c;
         for (int si = 0; si < nseg; ++si) {
             const uint32_t seg_addr = ptx::smem_addr(segs) + (uint32_t)(si * sizeof(DevSeg));
             if constexpr (TC) {
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
                     break;
                 }
             } else {
-                run_segment<T, R, NC, KU>(ptx::smem_addr(buf), seg_addr, ptx::smem_addr(gates), ctid, swz, c);
+                run_segment<T, R, NC, KU>(ptx::smem_addr(buf), seg_addr, ptx::smem_addr(gates), ctid, swz, c, origin);
             }
             if (si == nseg - 1) ptx::fence_proxy_async_smem();
             ptx::named_bar_sync(bar_id, NC);

@@ -44,7 +44,9 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         int32_t lq[2];  // labels in the gate's own order
         int32_t vq[2];  // virtual qubits
         uint64_t vmask;
+        bool diag;      // may join a section with qubits outside the chunk (diag_outside)
     };
+    const bool diag_outside = o.diag_outside != 0 && !o.use_tc;
 
     auto *plan = new sv_plan();
     plan->n = n;
@@ -77,6 +79,14 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         p.gi = i;
         p.nq = g.nq;
         p.vmask = 0;
+        p.diag = false;
+        if (diag_outside && (g.flags & SV_GATE_DIAG)) {
+            const int d = 1 << g.nq;
+            p.diag = true;
+            for (int r = 0; r < d; ++r)
+                for (int cc = 0; cc < d; ++cc)
+                    if (r != cc && (g.m[2 * (r * d + cc)] != 0.0 || g.m[2 * (r * d + cc) + 1] != 0.0)) p.diag = false;
+        }
         for (int j = 0; j < g.nq; ++j) {
             p.lq[j] = g.q[j];
             p.vq[j] = lab[g.q[j]];
@@ -114,13 +124,23 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         return chosen;
     };
     // Gates of REMAINING (at most `limit` inspected) that a section on `chosen` would take.
+    // Whether the QB_BLOCKED scan takes gate g into a section on `chosen` (see the scan below).
+    auto takes = [&](const PG &g, uint64_t chosen, uint64_t blocked, uint64_t out_blocked) {
+        const uint64_t outside = g.vmask & ~chosen;
+        return outside == 0 ? (g.vmask & blocked) == 0
+                            : g.diag && (g.vmask & chosen & blocked) == 0 && (outside & out_blocked) == 0;
+    };
     auto absorbed = [&](uint64_t chosen, size_t limit) {
-        uint64_t blocked = 0;
+        uint64_t blocked = 0, out_blocked = 0;
         int k = 0;
         for (size_t i = 0; i < remaining.size() && i < limit; ++i) {
             const PG &g = remaining[i];
-            if ((g.vmask & ~chosen) == 0 && (g.vmask & blocked) == 0) ++k;
-            else if (g.vmask & chosen) blocked |= g.vmask;
+            if (takes(g, chosen, blocked, out_blocked)) {
+                ++k;
+            } else {
+                if (g.vmask & chosen) blocked |= g.vmask;
+                out_blocked |= g.vmask & ~chosen;
+            }
         }
         return k;
     };
@@ -169,17 +189,18 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
                 cd.ce = popc(ch);
                 PlanOp tmp;
                 tmp.kind = 4;
-                uint64_t blocked = 0;
+                uint64_t blocked = 0, out_blocked = 0;
                 for (const PG &g : remaining) {
-                    if ((g.vmask & ~ch) == 0 && (g.vmask & blocked) == 0) {
+                    if (takes(g, ch, blocked, out_blocked)) {
                         BlockGate bg{};
                         bg.gi = g.gi;
                         bg.nq = g.nq;
                         for (int j = 0; j < g.nq; ++j) bg.phys[j] = m[g.vq[j]];
                         if (g.nq == 1) bg.phys[1] = -1;
                         tmp.gates.push_back(bg);
-                    } else if (g.vmask & ch) {
-                        blocked |= g.vmask;
+                    } else {
+                        if (g.vmask & ch) blocked |= g.vmask;
+                        out_blocked |= g.vmask & ~ch;
                     }
                 }
                 for (int v = 0; v < n; ++v)
@@ -222,10 +243,14 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         if (pinned)
             for (int v = 0; v < n; ++v)
                 if ((chosen >> v) & 1) block.mask |= 1ull << m[v];
-        uint64_t blocked = 0;
+        // diag_outside: a diagonal gate may also take qubits outside the chunk (constant over a
+        // chunk), provided no earlier deferred gate touches those qubits (OUT_BLOCKED), so the
+        // per-qubit gate order is kept
+        uint64_t blocked = 0, out_blocked = 0;
         next.clear();
         for (const PG &g : remaining) {
-            if ((g.vmask & ~chosen) == 0 && (g.vmask & blocked) == 0) {
+            const uint64_t outside = g.vmask & ~chosen;
+            if (takes(g, chosen, blocked, out_blocked)) {
                 BlockGate bg{};
                 bg.gi = g.gi;
                 bg.nq = g.nq;
@@ -238,6 +263,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             } else {
                 next.push_back(g);
                 if (g.vmask & chosen) blocked |= g.vmask;
+                out_blocked |= outside;
             }
         }
         plan->ops.push_back(std::move(block));
@@ -286,13 +312,11 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     // register groups per block (for statistics and execution)
     int nseg = 0;
     for (const PlanOp &op : plan->ops) {
-        if (op.kind == 2) nseg += (int)segment_block(op.gates, std::min(c, n), plan->seg_bits, 8).size();
+        if (op.kind == 2)
+            nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), plan->seg_bits, 8).size();
         if (op.kind == 4) {
             const GatherLayout L = gather_layout(op.mask, n, 8);
-            std::vector<BlockGate> loc = op.gates;
-            for (BlockGate &g : loc)
-                for (int j = 0; j < g.nq; ++j) g.phys[j] = L.local_of[g.phys[j]];
-            nseg += (int)segment_block(loc, L.ce, plan->seg_bits, 8).size();
+            nseg += (int)segment_block(localize_gates(op, n, c, &L), L.ce, plan->seg_bits, 8).size();
         }
     }
     plan->n_segments = nseg;
@@ -315,9 +339,10 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
     std::vector<HostSeg> segs;
     std::vector<int32_t> pending(gates.size());
     std::iota(pending.begin(), pending.end(), 0);
-    auto mask_of = [&](const BlockGate &g) {
-        uint64_t mk = 1ull << g.phys[0];
-        if (g.nq == 2) mk |= 1ull << g.phys[1];
+    auto mask_of = [&](const BlockGate &g) {  // chunk bits only (a qubit outside has phys -1)
+        uint64_t mk = 0;
+        for (int j = 0; j < g.nq; ++j)
+            if (g.phys[j] >= 0) mk |= 1ull << g.phys[j];
         return mk;
     };
     const int rr = std::min(r, width);
@@ -439,6 +464,20 @@ GatherLayout gather_layout(uint64_t mask, int n, int elem_bytes) {
     return L;
 }
 
+std::vector<BlockGate> localize_gates(const PlanOp &op, int n, int c, const GatherLayout *lay) {
+    const int width = std::min(c, n);
+    std::vector<BlockGate> loc = op.gates;
+    for (BlockGate &g : loc) {
+        for (int j = 0; j < g.nq; ++j) {
+            const int p = g.phys[j];
+            const int l = lay ? lay->local_of[p] : (p < width ? p : -1);
+            g.ext[j] = l < 0 ? p : -1;
+            g.phys[j] = l;
+        }
+    }
+    return loc;
+}
+
 template <typename T>
 void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevGate<T> &out) {
     auto local = [&](int phys) {
@@ -447,6 +486,49 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
         fail(SV_ERR_PLAN, "gate bit outside its register group");
     };
     std::memset(&out, 0, sizeof(out));
+    if (bg.ext[0] >= 0 || (g.nq == 2 && bg.ext[1] >= 0)) {
+        // diagonal gate with qubits outside the chunk: per value of the outside bits, the
+        // diagonal it leaves on its chunk qubit (or the phase it applies)
+        const int d = 1 << g.nq;
+        double D[8];
+        for (int i = 0; i < d; ++i) {
+            D[2 * i] = g.m[2 * (i * d + i)];
+            D[2 * i + 1] = g.m[2 * (i * d + i) + 1];
+        }
+        out.op = OP_DIAGX;
+        auto put = [&](int v, int i_lo, int i_hi) {
+            out.m[4 * v] = (T)D[2 * i_lo];
+            out.m[4 * v + 1] = (T)D[2 * i_lo + 1];
+            out.m[4 * v + 2] = (T)D[2 * i_hi];
+            out.m[4 * v + 3] = (T)D[2 * i_hi + 1];
+        };
+        int e0 = 0xFF, e1 = 0xFF;
+        // a phase is written as the diagonal (d, d) on register bit 0
+        if (g.nq == 1) {  // phase d[x], x = the qubit's bit
+            out.a = 0;
+            e0 = bg.ext[0];
+            put(0, 0, 0);
+            put(1, 1, 1);
+        } else if (bg.ext[0] >= 0 && bg.ext[1] >= 0) {  // phase d[x0 + 2 x1]
+            out.a = 0;
+            e0 = bg.ext[0];
+            e1 = bg.ext[1];
+            for (int v = 0; v < 4; ++v) put(v, v, v);
+        } else if (bg.ext[1] >= 0) {  // q0 in the chunk: diag(d[2x], d[1 + 2x]) on it
+            out.a = local(bg.phys[0]);
+            e0 = bg.ext[1];
+            put(0, 0, 1);
+            put(1, 2, 3);
+        } else {  // q1 in the chunk: diag(d[x], d[x + 2]) on it
+            out.a = local(bg.phys[1]);
+            e0 = bg.ext[0];
+            put(0, 0, 2);
+            put(1, 1, 3);
+        }
+        out.b = e0 | (e1 << 8);
+        out.code = out.a;
+        return;
+    }
     if (g.nq == 1) {
         out.a = local(bg.phys[0]);
         out.b = -1;
@@ -542,13 +624,14 @@ static bool gate_is_cheap(const sv_gate &g) {
 void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gates, int dtype, float *out) {
     for (int k = 0; k < kNumFeatures; ++k) out[k] = 0.f;
     const int n = plan.n;
-    std::vector<BlockGate> loc = op.gates;
+    std::vector<BlockGate> loc;
     int ce = std::min(plan.c, n);
     if (op.kind == 4) {
         const GatherLayout L = gather_layout(op.mask, n, 8);
-        for (BlockGate &g : loc)
-            for (int j = 0; j < g.nq; ++j) g.phys[j] = L.local_of[g.phys[j]];
+        loc = localize_gates(op, n, plan.c, &L);
         ce = L.ce;
+    } else {
+        loc = localize_gates(op, n, plan.c, nullptr);
     }
     const bool tc = plan.use_tc && dtype == SV_C64 && ce >= 11;
     const int r = tc ? 4 : (dtype == SV_C64 ? plan.seg_bits : 4);
@@ -560,6 +643,7 @@ void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gate
         cheap += gate_is_cheap(gates[g.gi]);
         for (int j = 0; j < g.nq; ++j) {
             const int p = g.phys[j];
+            if (p < 0) continue;  // outside the chunk
             hist[p < 4 ? p : (p < 8 ? 4 : 5)] += 1.f;
             ++q_total;
         }

@@ -29,8 +29,10 @@ enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_BOUNDS = 2 };
 struct BlockGate {
     int64_t gi;      // index into the caller's gate list
     int32_t nq;
-    int32_t phys[2]; // physical bit of the gate's q[0], q[1] (gate's own order)
+    int32_t phys[2]; // physical bit of the gate's q[0], q[1] (gate's own order); after
+                     // localize_gates: the chunk-local bit, or -1 for a qubit outside the chunk
     int32_t label[2];
+    int32_t ext[2] = {-1, -1};  // after localize_gates: state bit of a qubit outside the chunk
 };
 
 struct PlanOp {
@@ -100,7 +102,10 @@ enum : int32_t {
     OP_CXA = 5,    // exchange local states 1 <-> 3: control = lower bit a, target = b
     OP_CXB = 6,    // exchange 2 <-> 3: control = b, target = a
     OP_SWAP2 = 7,  // exchange 1 <-> 2
-    OP_X1 = 8      // 1-qubit bit flip
+    OP_X1 = 8,     // 1-qubit bit flip
+    OP_DIAGX = 9   // diagonal gate with qubits outside the chunk: b = e0 | e1 << 8 (state bits,
+                   // 0xFF = none); variant v = bit e0 + 2 bit e1 of the chunk's origin selects
+                   // m[4v..4v+3], a diagonal (d0, d1) on register bit a (a phase: d0 = d1, a = 0)
 };
 
 // Register group as the kernel reads it.  A thread's group index g enumerates the chunk bits
@@ -163,6 +168,11 @@ struct GatherLayout {
 };
 
 GatherLayout gather_layout(uint64_t mask, int n, int elem_bytes);
+
+// A section's gates on chunk-local bits: bits < min(c, n) for a contiguous chunk (kind 2), the
+// gathered layout's local order for kind 4 (`lay` non-null).  A qubit outside the chunk (only
+// diagonal gates, diag_outside) gets phys = -1 and its state bit in ext.
+std::vector<BlockGate> localize_gates(const PlanOp &op, int n, int c, const GatherLayout *lay);
 
 // Tensor-core path: per register group, the gates to fuse and where its B operand goes.
 struct ComposeSeg {

@@ -70,11 +70,12 @@ def test_quantum_volume_30_mirror_returns_to_zero(sv):
     assert abs(complex(got[0]) - 1.0) <= 1e-5 and err <= 1e-5, (complex(got[0]), err)
 
 
-def test_qft_28_closed_form_paper_layout(sv):
+@pytest.mark.parametrize("diag_outside", [0, 1])
+def test_qft_28_closed_form_paper_layout(sv, diag_outside):
     _need_host(24)
     n = 28
     x = cg.basis_index(n, 2)
-    got = _run(sv, n, cg.qft(n), "c128", basis=x, chunk_bits=12)
+    got = _run(sv, n, cg.qft(n), "c128", basis=x, chunk_bits=12, diag_outside=diag_outside)
     worst = 0.0
     piece = 1 << 24
     for s in range(0, 1 << n, piece):

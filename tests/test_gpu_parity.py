@@ -290,3 +290,27 @@ def test_tensor_core_quantum_volume_24(sv):
     ref = sim.simulate(n, desc)
     got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=13, gather_pinned=4, use_tc=1))
     assert_close(got, ref, "c64")
+
+
+def _diag_rich(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for g in cg.random_layers(n, 3, seed):
+        out.append(g)
+        a, b = (int(v) for v in rng.permutation(n)[:2])
+        out.append([("cz", (a, b), ()), ("cp", (a, b), (float(rng.uniform(0, 6.3)),)),
+                    ("rz", (a,), (float(rng.uniform(0, 6.3)),)), ("z", (b,), ())][int(rng.integers(0, 4))])
+    return out
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,c,pinned", [(12, 6, 0), (16, 10, 0), (16, 10, 4), (13, 8, 3), (20, 12, 4), (14, 5, 1)])
+def test_diag_outside_sections(sv, dtype, n, c, pinned):
+    """Diagonal gates applied inside sections whose chunk lacks some of their qubits (the chunk's
+    fixed bits select the diagonal): QFT of a basis state, a CZ-ladder ansatz and random layers
+    with CZ/CP/RZ/Z, both chunk layouts, against the oracle."""
+    x = cg.basis_index(n, 2)
+    for desc in (cg.qft(n), cg.hea(n, 3, n, 1), _diag_rich(n, n + c)):
+        ref = sim.simulate(n, desc, x)
+        assert_close(_run(sv, n, desc, dtype, basis=x,
+                          plan_opts=dict(chunk_bits=c, gather_pinned=pinned, diag_outside=1)), ref, dtype)

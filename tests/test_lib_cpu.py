@@ -152,3 +152,24 @@ def test_section_features_hand_computed():
     np.testing.assert_allclose(f[0], want, rtol=1e-6, atol=1e-7)
     f128 = plan.features(g, "c128")
     assert f128[0, 12] == 1.0
+
+
+@pytest.mark.parametrize("n,c,pinned", [(8, 3, 0), (12, 6, 0), (16, 10, 0), (12, 8, 4), (16, 10, 3), (30, 13, 4),
+                                        (28, 12, 0)])
+def test_planner_schedule_parity_diag_outside(sv, n, c, pinned):
+    """Both planners take the same diagonal gates into sections with qubits outside the chunk."""
+    import math
+    rng = np.random.Generator(np.random.PCG64(n * 100 + c))
+    mixed = []
+    for g in cg.random_layers(n, 3, n + c):
+        mixed.append(g)
+        a, b = (int(v) for v in rng.permutation(n)[:2])
+        mixed.append([("cz", (a, b), ()), ("cp", (a, b), (0.7,)), ("rz", (a,), (1.3,)), ("z", (b,), ())][int(rng.integers(0, 4))])
+    for desc in [cg.qft(n), cg.hea(n, 2, 3, 1), mixed] + _circuits(n, n + c):
+        gates = sv.make_gates(desc)
+        p = sv.Plan(n, gates, chunk_bits=c, gather_pinned=pinned, diag_outside=1)
+        q = planner.plan_blocking(n, desc, c, pinned=pinned, diag_outside=True)
+        assert p.serialize() == q.serialize()
+    qft = cg.qft(n)
+    p = sv.Plan(n, sv.make_gates(qft), chunk_bits=c, gather_pinned=pinned, diag_outside=1)
+    assert p.info().n_blocks == math.ceil((n - pinned) / (c - pinned))

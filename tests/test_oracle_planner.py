@@ -149,3 +149,44 @@ def test_gathered_chunks_validity_and_equivalence(n, c, pinned):
 def test_gathered_chunks_need_room():
     with pytest.raises(ValueError):
         planner.plan_blocking(8, [("cx", (0, 5), ())], 4, pinned=3)
+
+
+def _diag_circuits(n, seed):
+    """Circuits rich in diagonal gates: QFT (CP), a CZ ladder ansatz, random layers with CZ/CP/RZ/Z
+    sprinkled in."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mixed = []
+    for g in cg.random_layers(n, 3, seed):
+        mixed.append(g)
+        if rng.random() < 0.5:
+            a, b = (int(v) for v in rng.permutation(n)[:2])
+            r = int(rng.integers(0, 4))
+            mixed.append([("cz", (a, b), ()), ("cp", (a, b), (float(rng.uniform(0, 6.3)),)),
+                          ("rz", (a,), (float(rng.uniform(0, 6.3)),)), ("z", (b,), ())][r])
+    return [cg.qft(n), cg.hea(n, 3, seed, 0), mixed]
+
+
+@pytest.mark.parametrize("n,c,pinned", [(8, 3, 0), (10, 4, 0), (12, 6, 0), (10, 6, 3), (12, 8, 4), (9, 4, 1)])
+def test_diag_outside_validity_and_equivalence(n, c, pinned):
+    """Diagonal gates that join a section with qubits outside its chunk: the schedule stays valid
+    (every other gate inside its chunk, per-qubit order kept) and simulates to the same state."""
+    for gates in _diag_circuits(n, 11 * n + c):
+        p = planner.plan_blocking(n, gates, c, pinned=pinned, diag_outside=True)
+        planner.validate(p, gates, diag_outside=True)
+        ref = sim.simulate(n, gates, 5 % (1 << n))
+        assert np.abs(sim.execute_plan(n, gates, p, 5 % (1 << n)) - ref).max() < 1e-12
+        base = planner.plan_blocking(n, gates, c, pinned=pinned)
+        assert p.n_blocks <= base.n_blocks
+
+
+def test_diag_outside_qft_needs_one_section_per_chunk_of_hadamards():
+    """In the QFT every gate but the n Hadamards is a controlled phase, so with diag_outside a
+    section takes the Hadamards of its chunk qubits and every phase that touches them: the number
+    of sections is ceil(n / free chunk bits) with gathered chunks (here 16 qubits, chunk 8 with 2
+    pinned bits -> 6 free -> 3 sections), against one section per few Hadamards otherwise."""
+    gates = cg.qft(16)
+    for n, c, pinned in ((16, 8, 2), (16, 8, 0), (16, 5, 1)):
+        p = planner.plan_blocking(n, gates, c, pinned=pinned, diag_outside=True)
+        base = planner.plan_blocking(n, gates, c, pinned=pinned)
+        assert p.n_blocks == math.ceil((n - pinned) / (c - pinned)), (c, pinned, p.n_blocks)
+        assert p.n_blocks < base.n_blocks
