@@ -2,9 +2,10 @@
 """Benchmark of the cache-blocked state-vector simulator on GB300.
 
 Workload (default): quantum-volume circuit, n = 30 qubits, depth 30 (450 Haar SU(4) gates),
-complex64 state (8 GiB), chunk c = 13.  One step = build the gate records, plan the cache
-blocking (host), reset the state to |0..0>, apply the circuit on the cache-blocked path, and
-read the norm back.  Metric: gates per second (higher is better), plus effective HBM bandwidth
+complex64 state (8 GiB), chunk c = 13 gathered with 4 pinned bits, tensor-core register groups,
+look-ahead chunk choice (the paper's rule is timed alongside).  One step = build the gate
+records, plan the cache blocking (host), reset the state to |0..0>, apply the circuit on the
+cache-blocked path, and read the norm back.  Metric: gates per second (higher is better), plus effective HBM bandwidth
 = (blocking sweeps + permutation sweeps) x 2 x 2^n x 8 B / time.
 
 Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle on a bounded sample of
@@ -540,11 +541,16 @@ def run_ours(args):
     model, model_info = None, None
     if args.planner == "steered":
         model, model_info = _train_cost_model(sv, st, w, plan_opts)
+    if args.planner == "lookahead":
+        plan_opts["lookahead"] = 1
     st.set_profiling(True)
+
+    rule_opts = {k: v for k, v in plan_opts.items() if k != "lookahead"}
 
     def step(use_model=True):
         gates = sv.make_gates(desc)
-        plan = sv.Plan(n, gates, model=model if use_model else None, **plan_opts)
+        plan = (sv.Plan(n, gates, model=model, **plan_opts) if use_model
+                else sv.Plan(n, gates, **rule_opts))
         st.init_basis(0)
         st.apply(gates, plan)
         nrm = st.norm2()
@@ -604,7 +610,7 @@ def run_ours(args):
 
     # the paper's rule-based planner on the same workload, for comparison with the steered one
     rule = None
-    if model is not None:
+    if args.planner != "rule":
         rule_info = None
         for _ in range(1):
             step(use_model=False)
@@ -701,8 +707,9 @@ def main():
     ap.add_argument("--tc", type=int, default=1, help="1: fused register groups on the tensor cores (3xTF32)")
     ap.add_argument("--gather-pinned", type=int, default=4,
                     help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
-    ap.add_argument("--planner", default="steered", choices=["rule", "steered"],
-                    help="steered: the learned cost model picks each section's chunk (trained before timing)")
+    ap.add_argument("--planner", default="lookahead", choices=["rule", "lookahead", "steered"],
+                    help="rule: the paper's chunk choice; lookahead: the chunk that takes the most gates; "
+                         "steered: the learned cost model picks among both and smaller chunks (trained before timing)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-gates-per-step", type=int, default=4)
     args = ap.parse_args()

@@ -88,7 +88,11 @@ typedef struct sv_options {
                                join a section while some of their qubits lie outside its chunk: those
                                qubits are constant over a chunk, so the gate acts there as a diagonal
                                on its chunk qubits (or a phase).  Ignored with use_tc.  default 0 */
-    int32_t reserved[7];
+    int32_t lookahead;      /* 1 (gathered chunks): choose each section's chunk by look-ahead -- grow it
+                               from the pinned bits and the first gate by the pending gate whose qubits
+                               let the section take the most gates -- instead of the paper's priority
+                               rule.  A heuristic of this library, not the paper's.  default 0 */
+    int32_t reserved[6];
 } sv_options;
 
 void sv_options_default(sv_options *opts);

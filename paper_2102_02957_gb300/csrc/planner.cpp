@@ -178,7 +178,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     std::vector<SectionCandidate> cands;
     while (!remaining.empty()) {
         // choose QB_CHUNK
-        uint64_t chosen = rule_select(target);
+        uint64_t chosen = (pinned && o.lookahead && !chooser) ? greedy_select(target) : rule_select(target);
         if (chooser && pinned) {
             cands.clear();
             auto add_candidate = [&](uint64_t ch) {

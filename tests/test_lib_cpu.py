@@ -9,7 +9,7 @@ import pytest
 
 import circuitgen as cg
 from oracle import gates as og
-from oracle import planner
+from oracle import planner, sim
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -173,3 +173,44 @@ def test_planner_schedule_parity_diag_outside(sv, n, c, pinned):
     qft = cg.qft(n)
     p = sv.Plan(n, sv.make_gates(qft), chunk_bits=c, gather_pinned=pinned, diag_outside=1)
     assert p.info().n_blocks == math.ceil((n - pinned) / (c - pinned))
+
+
+def _plan_from_stream(stream, pinned):
+    """The library's serialised schedule as an oracle Plan (same integer format)."""
+    it = iter(stream)
+    n, c, reserve, restore, nops = (next(it) for _ in range(5))
+    plan = planner.Plan(n=n, c=c, reserve=reserve, restore_layout=bool(restore), pinned=pinned)
+    for _ in range(nops):
+        kind = next(it)
+        if kind in (1, 3):
+            cnt = next(it)
+            plan.ops.append(("swap" if kind == 1 else "unpermute", [(next(it), next(it)) for _ in range(cnt)]))
+        else:
+            mask = next(it) if kind == 4 else None
+            cnt = next(it)
+            body = []
+            for _ in range(cnt):
+                gi, nq, p0, p1 = next(it), next(it), next(it), next(it)
+                body.append((gi, (p0,) if nq == 1 else (p0, p1)))
+            plan.ops.append(("gblock", (mask, body)) if kind == 4 else ("block", body))
+    plan.final_map = list(it)
+    return plan
+
+
+@pytest.mark.parametrize("n,c,pinned", [(10, 6, 2), (12, 8, 4), (14, 9, 3)])
+def test_lookahead_plans_valid_and_equivalent(sv, n, c, pinned):
+    """The look-ahead chunk choice (a heuristic of this library, not the paper's rule) yields valid
+    schedules that simulate to the original circuit, with no more sections than the rule on
+    these circuits; checked on the oracle side (no GPU)."""
+    for desc in _circuits(n, 5 * n + c):
+        gates = sv.make_gates(desc)
+        for diag in (0, 1):
+            p = sv.Plan(n, gates, chunk_bits=c, gather_pinned=pinned, lookahead=1, diag_outside=diag)
+            q = _plan_from_stream(p.serialize(), pinned)
+            planner.validate(q, desc, diag_outside=bool(diag))
+            ref = sim.simulate(n, desc, 3)
+            assert np.abs(sim.execute_plan(n, desc, q, 3) - ref).max() < 1e-12
+    qv = cg.quantum_volume(n, 8, n)
+    g = sv.make_gates(qv)
+    assert (sv.Plan(n, g, chunk_bits=c, gather_pinned=pinned, lookahead=1).info().n_blocks
+            <= sv.Plan(n, g, chunk_bits=c, gather_pinned=pinned).info().n_blocks)
