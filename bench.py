@@ -380,8 +380,10 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     states = [sv.StateVector(n, "c64", stream=stream) for n in ns]
     base = {} if not args.chunk_bits else dict(chunk_bits=args.chunk_bits)
+    if args.planner == "lookahead":
+        base["lookahead"] = 1
     if args.chunk_bits:
-        best, tune_ms = dict(chunk_bits=args.chunk_bits), None
+        best, tune_ms = dict(base), None
     else:
         best, tune_ms = sv.batch_tune(states, gates, **base)
     b = sv.Batch(states, gates, **best)
@@ -478,7 +480,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {len(ns)} states, n={min(ns)}..{max(ns)}, {G} gates, "
                                    f"{sum(2 ** n for n in ns) * 8 / 2 ** 30:.1f} GiB complex64",
-                       "chunk_bits": best.get("chunk_bits"), "tuned_ms": tune_ms, "work_items": items,
+                       "chunk_bits": best.get("chunk_bits"), "planner": "lookahead" if best.get("lookahead") else "rule",
+                       "tuned_ms": tune_ms, "work_items": items,
                        "sections": sections, "graph": True, "from_zero": True,
                        "l2": "10 GiB of states >> 129 MB L2 (no flush needed)"},
             "roofline": roofline, "sequential_blocked_ms": seq_ms,
