@@ -36,7 +36,7 @@ typedef enum sv_status {
     SV_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed                    */
     SV_ERR_PLAN = 4,        /* plan does not match the state / gate list, or planning failed   */
     SV_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired; the state is undefined      */
-    SV_ERR_UNSUPPORTED = 6  /* valid request that this build does not implement                */
+    SV_ERR_UNSUPPORTED = 6  /* valid request that the library does not implement              */
 } sv_status;
 
 typedef enum sv_dtype {

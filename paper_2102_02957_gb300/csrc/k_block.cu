@@ -1,25 +1,30 @@
 // Blocking section: one HBM sweep applies every gate of the section to every chunk
-// (Sec. IV.C, Listing 4: "for all chunks: fetch chunk, apply each gate of the section, swap
-// out").  On one GPU the chunk of 2^c amplitudes (physical bits 0..c-1, contiguous) is the
-// unit staged from HBM into shared memory; the transpiler (Sec. IV.A) guarantees that every
-// gate of the section acts on chunk bits only.
+// (Sec. IV.C, Listing 4: for all chunks, fetch the chunk, apply each gate of the section, write
+// it back).  On one GPU the chunk of 2^c amplitudes is the unit staged from HBM into shared
+// memory: either the contiguous chunk j (physical bits 0..c-1 after the paper's chunk_swap
+// rounds) or a gathered chunk (any c bits including the low pinned ones, fetched in place by
+// rank <= 5 tensor copies).  The transpiler (Sec. IV.A) guarantees that every gate of the section
+// acts on chunk bits only -- except diagonal gates planned with diag_outside, whose outside bits
+// are read off the chunk's origin index.
 //
 // Kernel organisation (persistent, warp-specialised):
-//  * warp 0, lane 0 is the producer: it streams the CTA's chunks j = blockIdx.x + t*gridDim.x
-//    into a ring of NBUF shared-memory buffers with 1-D bulk asynchronous copies (TMA engine)
-//    completing on "full" mbarriers;
-//  * the other NC threads are consumers.  For each chunk they run the section's register
-//    groups: each thread loads the 2^R amplitudes spanned by the group's R chunk bits from
-//    shared memory into registers, applies every gate of the group there, and stores them
-//    back.  Then one consumer writes the chunk back with a bulk copy and releases the buffer
-//    to the producer through an "empty" mbarrier once the write-back has read it.
+//  * warp 0, lane 0 is the producer (produce_chunks): it streams the CTA's chunks
+//    j = blockIdx.x + t*gridDim.x into a ring of shared-memory buffers with bulk or tensor
+//    asynchronous copies (TMA engine) completing on "full" mbarriers;
+//  * two consumer groups of NC threads take alternate chunks, so one group's shared-memory and
+//    barrier phases overlap the other's arithmetic.  For each chunk a group runs the section's
+//    register groups -- SIMT (run_segment: each thread loads the 2^R amplitudes spanned by the
+//    group's R chunk bits into registers, applies every gate of the group there, stores them
+//    back) or tensor cores (run_segment_tc: the group's fused unitary applied to 128-row tiles
+//    with tcgen05 MMAs) -- then one consumer writes the chunk back (store_chunk) and releases the
+//    buffer to the producer through an "empty" mbarrier once the write-back has read it.
 //
 // Shared-memory layout of a chunk while it is being worked on: amplitude i sits in slot
 // i ^ F(i), where F XORs a fixed non-zero pattern V[k] into the low slot bits for every set
-// bit k >= SB of i (SB = log2 of the amplitudes per 128-byte row).  The bulk copies move the
-// natural layout, so the first group reads and the last group writes unswizzled slots.  For
-// every group the host picks which chunk bits the lanes of a half-warp (quarter-warp for
-// complex128) enumerate so that their slots fall in distinct banks.
+// bit k >= SB of i (SB = log2 of the amplitudes per 128-byte row).  The copies move the natural
+// layout, so the first group reads and the last group writes unswizzled slots.  For every group
+// the host picks which chunk bits the lanes of a half-warp (quarter-warp for complex128)
+// enumerate so that their slots fall in distinct banks.
 //
 // Every wait is bounded (globaltimer); on expiry the kernel records DEV_ERR_TIMEOUT in the
 // error word and stops.
