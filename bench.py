@@ -382,6 +382,7 @@ def run_batch(args):
     base = {} if not args.chunk_bits else dict(chunk_bits=args.chunk_bits)
     if args.planner == "lookahead":
         base["lookahead"] = 1
+    base["use_tc"] = int(args.batch_tc)
     if args.chunk_bits:
         best, tune_ms = dict(base), None
     else:
@@ -414,17 +415,20 @@ def run_batch(args):
     value = world * G * args.steps / (elapsed_ms / 1000.0)
     peak, peak_kind = _peaks()
     achieved = nbytes / (ms_step / 1000.0) / 1e9
-    # the batch is bound by FP32 arithmetic, not HBM: its roofline is the FMA pipes
+    # SIMT sections are bound by FP32 arithmetic (the FMA pipes); with tensor-core sections the
+    # arithmetic moves to the tensor pipes and the sweep's bytes are the bound in principle
     flops = 2.0 * _algorithmic_fma(ns, descs)
     alu_peak = _fp32_peak_tflops()
     achieved_tf = flops / (ms_step / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_batch", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak,
-                "peak_source": "derived: SMs x 128 FP32 FMA lanes x 2 flops x max SM clock (MEASURED_PEAKS.json)",
-                "traffic": _traffic_for("paper_2102_02957_gb300/csrc/k_batch.cu", args.workload),
-                "algorithmic_flops_per_launch": flops, "launch_ms": ms_step,
-                "hbm": {"algorithmic_bytes_per_launch": nbytes, "achieved_GBs": achieved, "peak_GBs": peak,
-                        "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"}}
+    alu = {"achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
+           "peak_source": "derived: SMs x 128 FP32 FMA lanes x 2 flops x max SM clock (MEASURED_PEAKS.json)",
+           "algorithmic_flops_per_launch": flops}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": nbytes}
+    main, other = (hbm, alu) if best.get("use_tc") else (alu, hbm)
+    roofline = dict(main, bound="hbm" if best.get("use_tc") else "alu", kernel="k_batch",
+                    traffic=_traffic_for("paper_2102_02957_gb300/csrc/k_batch.cu", args.workload), launch_ms=ms_step,
+                    other={"bound": "alu" if best.get("use_tc") else "hbm", **other})
     norms = [s.norm2() for s in states[:: max(1, len(states) // 16)]]
 
     # the same circuits one state after another on the single-state blocked path
@@ -481,6 +485,7 @@ def run_batch(args):
             "config": {"workload": f"{args.workload}: {len(ns)} states, n={min(ns)}..{max(ns)}, {G} gates, "
                                    f"{sum(2 ** n for n in ns) * 8 / 2 ** 30:.1f} GiB complex64",
                        "chunk_bits": best.get("chunk_bits"), "planner": "lookahead" if best.get("lookahead") else "rule",
+                       "tensor_cores": bool(best.get("use_tc")),
                        "tuned_ms": tune_ms, "work_items": items,
                        "sections": sections, "graph": True, "from_zero": True,
                        "l2": "10 GiB of states >> 129 MB L2 (no flush needed)"},
@@ -708,6 +713,8 @@ def main():
     ap.add_argument("--seg-bits", type=int, default=4, help="register-group width inside a chunk (4 or 5)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the workload's chunk bits")
     ap.add_argument("--tc", type=int, default=1, help="1: fused register groups on the tensor cores (3xTF32)")
+    ap.add_argument("--batch-tc", type=int, default=1,
+                    help="batched workloads: 1 runs sections of >= 11 chunk bits on the tensor cores (128-thread CTAs)")
     ap.add_argument("--gather-pinned", type=int, default=4,
                     help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
     ap.add_argument("--planner", default="lookahead", choices=["rule", "lookahead", "steered"],

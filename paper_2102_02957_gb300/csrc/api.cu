@@ -143,6 +143,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::ve
             host.resize(host.size() + (size_t)bp.nseg * TC_B_BYTES, 0);
             for (size_t k = p0; k < p1; ++k) {
                 ComposeSeg c{};
+                c.flag_off = kNoFlag;
                 c.g0 = (int32_t)dg.size();
                 for (int32_t gi : segs[k].gates) {
                     DevGate<double> g;

@@ -16,6 +16,7 @@ struct sv_batch {
     int nops = 0;
     int64_t total = 0;
     double bytes = 0;
+    int use_tc = 0;
     cudaGraph_t graph[2] = {nullptr, nullptr};     // per SV_BATCH_FROM_ZERO value
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<std::pair<void *, int>> idle;       // states without gates: (amplitudes, n)
@@ -46,7 +47,7 @@ void launch_once(sv_batch *b, int from_zero) {
     int *err = reinterpret_cast<int *>(next + 1);
     launch_batch(b->dev + b->off_ops, b->nops, b->dev + b->off_progs,
                  reinterpret_cast<void *const *>(b->dev + b->off_amps), ops_done, chunks_done, next, b->total,
-                 from_zero, err, b->work);
+                 from_zero, b->use_tc, err, b->work);
 }
 
 int *batch_err(sv_batch *b) {
@@ -95,6 +96,10 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
     if (opts) base = *opts; else sv_options_default(&base);
     std::vector<std::vector<BatchOp>> per_state((size_t)count);
     std::vector<unsigned char> progs;
+    // tensor-core sections (complex64 chunks of >= 11 bits): groups fused in FP64 on the GPU
+    const bool want_tc = base.use_tc != 0;
+    std::vector<ComposeSeg> compose;
+    std::vector<DevGate<double>> compose_gates;
     auto align = [&](size_t a) {
         while (progs.size() % a) progs.push_back(0);
     };
@@ -115,7 +120,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
             if (gates[s][i].flags & SV_GATE_SWAP)
                 fail(SV_ERR_UNSUPPORTED, "sv_batch_create: SWAP relabels are not batched");
         o.seg_bits = 4;
-        o.use_tc = 0;
+        o.use_tc = 0;  // the planner's own tensor-core rules do not apply to batch sections
         std::unique_ptr<sv_plan> plan(plan_blocking(h->n, gates[s], n_gates[s], o));
         if (plan->ops.empty()) b->idle.emplace_back(h->amp, h->n);
         int opno = 0;
@@ -159,22 +164,26 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                 }
             }
             // the section's program in pieces of at most kBatchMaxProgBytes, each a 16-byte header
-            // {nseg, ngate, bytes, 0} + register groups + gate records; the kernel runs the
-            // pieces one after another on the resident chunk
+            // {nseg, ngate, bytes, 0} + register groups + gate records (SIMT) or the groups' B
+            // operands and unitarity flags (tensor cores); the kernel runs the pieces one after
+            // another on the resident chunk
+            const bool tc = want_tc && k >= 11;
             align(256);
             BatchOp sec = bo;
             sec.op = opno++;
             sec.prog_off = (uint32_t)progs.size();
             sec.npiece = 0;
+            sec.tc = tc ? 1 : 0;
             size_t p0 = 0;
             while (p0 < segs.size()) {
                 size_t p1 = p0, gates_in = 0;
                 while (p1 < segs.size()) {
                     const size_t g_next = gates_in + segs[p1].gates.size();
-                    const size_t bytes =
-                        16 + ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + g_next * sizeof(DevGate<float>);
-                    if (bytes > (size_t)kBatchMaxProgBytes && p1 > p0) break;
-                    if (bytes > (size_t)kBatchMaxProgBytes) fail(SV_ERR_UNSUPPORTED, "register group too large");
+                    const size_t body = tc ? (p1 + 1 - p0) * (size_t)kBatchTcGroupBytes : g_next * sizeof(DevGate<float>);
+                    const size_t bytes = 16 + ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + body;
+                    const size_t limit = want_tc ? (size_t)kBatchMaxProgBytesTc : (size_t)kBatchMaxProgBytes;
+                    if (bytes > limit && p1 > p0) break;
+                    if (bytes > limit) fail(SV_ERR_UNSUPPORTED, "register group too large");
                     gates_in = g_next;
                     ++p1;
                 }
@@ -192,10 +201,12 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                     // the chunk arrives and leaves in the natural layout
                     d.flags = (int8_t)((q == 0 ? 1 : 0) | (q + 1 == segs.size() ? 2 : 0));
                     d.g0 = (int16_t)dg.size();
-                    for (int32_t gi : hs.gates) {
-                        DevGate<float> g;
-                        encode_gate<float>(gates[s][loc[gi].gi], loc[gi], hs, g);
-                        dg.push_back(g);
+                    if (!tc) {
+                        for (int32_t gi : hs.gates) {
+                            DevGate<float> g;
+                            encode_gate<float>(gates[s][loc[gi].gi], loc[gi], hs, g);
+                            dg.push_back(g);
+                        }
                     }
                     d.g1 = (int16_t)dg.size();
                     ds.push_back(d);
@@ -205,8 +216,25 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                 const unsigned char *p = reinterpret_cast<const unsigned char *>(ds.data());
                 progs.insert(progs.end(), p, p + ds.size() * sizeof(DevSeg));
                 align(16);
-                p = reinterpret_cast<const unsigned char *>(dg.data());
-                progs.insert(progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
+                if (tc) {
+                    for (size_t q = p0; q < p1; ++q) {  // B operands, written by the compose kernel
+                        ComposeSeg cs{};
+                        cs.b_off = (uint32_t)progs.size();
+                        cs.flag_off = cs.b_off + TC_B_BYTES;
+                        cs.g0 = (int32_t)compose_gates.size();
+                        for (int32_t gi : segs[q].gates) {
+                            DevGate<double> g;
+                            encode_gate<double>(gates[s][loc[gi].gi], loc[gi], segs[q], g);
+                            compose_gates.push_back(g);
+                        }
+                        cs.g1 = (int32_t)compose_gates.size();
+                        compose.push_back(cs);
+                        progs.resize(progs.size() + kBatchTcGroupBytes, 0);
+                    }
+                } else {
+                    p = reinterpret_cast<const unsigned char *>(dg.data());
+                    progs.insert(progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
+                }
                 align(16);
                 const int32_t hd[4] = {(int32_t)ds.size(), (int32_t)dg.size(), (int32_t)(progs.size() - at), 0};
                 std::memcpy(progs.data() + at, hd, sizeof(hd));
@@ -262,6 +290,24 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
     if (!progs.empty())
         check_cuda(cudaMemcpy(b->dev + b->off_progs, progs.data(), progs.size(), cudaMemcpyHostToDevice), "H2D");
     check_cuda(cudaMemcpy(b->dev + b->off_amps, amps.data(), amps.size() * sizeof(void *), cudaMemcpyHostToDevice), "H2D");
+    if (!compose.empty()) {  // fuse every tensor-core group into its B operand, once per batch
+        unsigned char *tmp = nullptr;
+        const size_t cs_bytes = compose.size() * sizeof(ComposeSeg);
+        const size_t g_bytes = compose_gates.size() * sizeof(DevGate<double>);
+        check_cuda(cudaMalloc(&tmp, cs_bytes + g_bytes + 256), "cudaMalloc(compose)");
+        check_cuda(cudaMemcpy(tmp, compose.data(), cs_bytes, cudaMemcpyHostToDevice), "H2D");
+        unsigned char *gdev = tmp + ((cs_bytes + 255) & ~size_t(255));
+        if (g_bytes) check_cuda(cudaMemcpy(gdev, compose_gates.data(), g_bytes, cudaMemcpyHostToDevice), "H2D");
+        try {
+            launch_compose(tmp, (int)compose.size(), gdev, b->dev + b->off_progs, nullptr, b->work);
+            check_cuda(cudaStreamSynchronize(b->work), "cudaStreamSynchronize");
+        } catch (...) {
+            cudaFree(tmp);
+            throw;
+        }
+        cudaFree(tmp);
+        b->use_tc = 1;
+    }
     *out = b.release();
     SV_API_END
 }

@@ -4,6 +4,7 @@
 #pragma once
 #include <stdint.h>
 
+#include "ptx.cuh"
 #include "sv_internal.h"
 
 namespace sv {
@@ -63,6 +64,11 @@ __device__ __forceinline__ int lds_s8(uint32_t a) {
 __device__ __forceinline__ int lds_s16(uint32_t a) {
     int v;
     asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int lds_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ void ldc_i4(uint32_t a, int &x, int &y, int &z, int &w) {
@@ -361,6 +367,168 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
             }
         }
     }
+}
+
+constexpr uint64_t kTcWaitLimitNs = 4000000000ull;  // bounded waits of the tensor-core groups (4 s)
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Tensor-core register group (complex64, 4 bits): the group's fused unitary, stored as the
+// real-embedded B operand (B_hi at `bhi`, B_lo at bhi + 4096), is applied on tiles of 128
+// register groups: every thread writes its group's 32 reals split into TF32 high and low parts
+// to its TMEM lane (A_hi, A_lo), one thread issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo
+// (3 x 4 MMAs, M = 128, N = K = 32, FP32 accumulation), and every thread reads its row of D back.
+// Two tiles are in flight per group; TMEM columns of tile buffer k: A_hi [tcol + 96k, +32),
+// A_lo [+32, +64), D [+64, +96); `mbar[k]` signals its MMAs' completion.
+//
+// RENORM: the tensor cores' FP32 accumulation truncates, shrinking each result by a few units
+// in the last place the same way every time.  Callers that cannot restore the state's norm once
+// per circuit set RENORM: for a group whose fused matrix is unitary (the int after B_lo is
+// nonzero) each output row is rescaled to its input row's norm, as y <- y (1 + d) with
+// d = (|x|^2 - |y|^2) / (2 |y|^2) (a scale factor rounded next to 1 would itself be biased).
+template <int NC, bool RENORM = false>
+__device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint32_t bhi, int ctid, const int *swz,
+                                               int c, uint32_t tcol, int bar_id, uint64_t *mbar, uint32_t (&phase)[2],
+                                               volatile int *abort_flag) {
+    constexpr int R = 4, NA = 16;
+    int po[R], pf[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int p = lds_s8(seg + j);
+        po[j] = 1 << p;
+        pf[j] = po[j] ^ swz[p];
+    }
+    const int lane = ctid & 31;
+    int lbase = 0, lfb = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int p = lds_s8(seg + 8 + j);
+        if ((lane >> j) & 1) { lbase |= 1 << p; lfb ^= swz[p]; }
+    }
+    const int nrest = lds_s8(seg + 13), flags = lds_s8(seg + 14);
+    int rpo[kMaxRest], rpf[kMaxRest];
+#pragma unroll
+    for (int j = 0; j < kMaxRest; ++j) {
+        const int p = j < nrest ? lds_s8(seg + 16 + j) : 0;
+        rpo[j] = j < nrest ? 1 << p : 0;
+        rpf[j] = j < nrest ? swz[p] : 0;
+    }
+    const int T = (1 << (c - R)) / NC;  // 128-row tiles per chunk
+    const uint32_t lane_off = (uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16;  // this thread's TMEM lane
+    constexpr uint32_t idesc = ptx::idesc_tf32(128, 32);
+
+    // group base (natural and swizzled) of this thread's row in tile t
+    auto row_base = [&](int t, int &base, int &sbase) {
+        const int hi = (t * NC + ctid) >> 5;
+        int bs = lbase, fb = lfb;
+#pragma unroll
+        for (int j = 0; j < kMaxRest; ++j)
+            if ((hi >> j) & 1) { bs |= rpo[j]; fb ^= rpf[j]; }
+        base = bs;
+        sbase = bs ^ fb;
+    };
+    // byte steps between the group's amplitudes in Gray-code order (the natural and the
+    // swizzled address are both linear in the group index over GF(2)), load and store side
+    uint32_t ld_step[R], st_step[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        ld_step[j] = (uint32_t)((flags & 1) ? po[j] : pf[j]) << 3;
+        st_step[j] = (uint32_t)((flags & 2) ? po[j] : pf[j]) << 3;
+    }
+    // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
+    // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
+    bool failed = false;
+    const bool renorm = RENORM && lds_s32(bhi + 8192) != 0;
+    auto stage = [&](int t, int k, int &base, int &sbase, float &nrm) -> bool {
+        row_base(t, base, sbase);
+        uint32_t ahi[32], alo[32];
+        nrm = 0.f;
+        // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
+        // buffer base is only 1 KiB aligned, so it is added after the XOR walk, never XORed
+        uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            if (b) off ^= ld_step[__ffs(b) - 1];
+            const int gidx = b ^ (b >> 1);  // Gray code: this amplitude's local index
+            float xr, xi;
+            SM<float>::ld(buf + off, xr, xi);
+            ahi[2 * gidx] = __float_as_uint(xr);
+            ahi[2 * gidx + 1] = __float_as_uint(xi);
+            alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u));
+            alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u));
+            if (RENORM) nrm = fmaf(xr, xr, fmaf(xi, xi, nrm));
+        }
+        const uint32_t col = tcol + (uint32_t)k * 96;
+        ptx::tmem_st32(col + lane_off, ahi);
+        ptx::tmem_st32(col + 32 + lane_off, alo);
+        ptx::tmem_wait_st();
+        ptx::tc_fence_before();
+        // every row of the tile is in TMEM; the barrier also tells the group whether any
+        // thread's wait for an earlier tile expired
+        if (ptx::named_bar_or(bar_id, NC, failed)) return false;
+        if (ctid == 0) {
+            ptx::tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, s > 0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 32 + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, 1);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 4096 + 256 * s, 128, 1024), idesc,
+                                 1);
+            ptx::mma_commit(&mbar[k]);
+        }
+        return true;
+    };
+    // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
+    // (after an expired wait the tile is garbage; the group stops at its next barrier)
+    auto finish = [&](int k, int base, int sbase, float nrm) {
+        if (!ptx::mbar_wait(&mbar[k], phase[k], kTcWaitLimitNs)) {
+            failed = true;
+            *abort_flag = 1;
+        }
+        phase[k] ^= 1;
+        ptx::tc_fence_after();
+        uint32_t y[32];
+        ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
+        ptx::tmem_wait_ld();
+        if (RENORM && renorm) {
+            float ny = 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) ny = fmaf(__uint_as_float(y[q]), __uint_as_float(y[q]), ny);
+            const float d = ny > 0.f ? 0.5f * (nrm - ny) / ny : 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) y[q] = __float_as_uint(fmaf(__uint_as_float(y[q]), d, __uint_as_float(y[q])));
+        }
+        uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            if (b) off ^= st_step[__ffs(b) - 1];
+            const int gidx = b ^ (b >> 1);
+            SM<float>::st(buf + off, __uint_as_float(y[2 * gidx]), __uint_as_float(y[2 * gidx + 1]));
+        }
+    };
+    // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
+    int pb, ps;
+    float pn;
+    if (!stage(0, 0, pb, ps, pn)) return false;
+    for (int t = 1; t < T; ++t) {
+        int nb, ns;
+        float nn;
+        if (!stage(t, t & 1, nb, ns, nn)) return false;
+        finish((t - 1) & 1, pb, ps, pn);
+        pb = nb;
+        ps = ns;
+        pn = nn;
+    }
+    finish((T - 1) & 1, pb, ps, pn);
+    return !ptx::named_bar_or(bar_id, NC, failed);  // the group leaves together
 }
 
 }  // namespace

@@ -99,7 +99,9 @@ __global__ void k_compose_f64(const ComposeSeg *__restrict__ segs, const DevGate
     }
     atomicMax(&dev_bits, (unsigned long long)__double_as_longlong(worst));  // non-negative: order as integers
     __syncthreads();
-    if (j == 0 && !(__longlong_as_double((long long)dev_bits) <= 1e-10)) atomicAnd(all_unitary, 0);
+    const bool unitary = __longlong_as_double((long long)dev_bits) <= 1e-10;
+    if (j == 0 && !unitary && all_unitary) atomicAnd(all_unitary, 0);
+    if (j == 0 && sg.flag_off != kNoFlag) *reinterpret_cast<int *>(prog + sg.flag_off) = unitary ? 1 : 0;
     // column j of U is (vr, vi); write B entries with input index c = j
     unsigned char *bhi = prog + sg.b_off, *blo = bhi + 4096;
     for (int r = 0; r < 16; ++r) {

@@ -176,10 +176,11 @@ std::vector<BlockGate> localize_gates(const PlanOp &op, int n, int c, const Gath
 
 // Tensor-core path: per register group, the gates to fuse and where its B operand goes.
 struct ComposeSeg {
-    int32_t g0, g1;   // gate range in the FP64 gate array
-    uint32_t b_off;   // byte offset of the group's B_hi (B_lo follows at +4096) in the program
-    int32_t pad;
+    int32_t g0, g1;     // gate range in the FP64 gate array
+    uint32_t b_off;     // byte offset of the group's B_hi (B_lo follows at +4096) in the program
+    uint32_t flag_off;  // where to write an int: 1 if the fused matrix is unitary (kNoFlag: none)
 };
+constexpr uint32_t kNoFlag = 0xFFFFFFFFu;
 constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
 
 // Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
@@ -190,18 +191,20 @@ struct BatchOp {
     int32_t state, op, ce, low;
     int64_t nchunks, first;  // chunks of this section; first global work-item index
     uint32_t prog_off, prog_bytes;
-    int32_t npiece, pad;
+    int32_t npiece, tc;  // tc: tensor-core groups (pieces hold B operands instead of gate records)
     int32_t nhigh, nouter;
     int8_t high[24];
     int8_t outer[40];
 };
 constexpr int kBatchMaxChunkBits = 13;
-constexpr int kBatchMaxProgBytes = 24 * 1024;
+constexpr int kBatchMaxProgBytes = 24 * 1024;    // program piece of a SIMT batch
+constexpr int kBatchMaxProgBytesTc = 32 * 1024;  // ... of a batch with tensor-core sections (per pool)
+constexpr int kBatchTcGroupBytes = TC_B_BYTES + 16;  // B operand + unitarity flag per group
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
-                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int *dev_err,
-                  cudaStream_t st);
-// Fuse the register groups in FP64; *all_unitary (1 on entry) is cleared when a fused matrix
-// is not unitary to 1e-10 (max |U^H U - I|).
+                  int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int use_tc,
+                  int *dev_err, cudaStream_t st);
+// Fuse the register groups in FP64; *all_unitary (1 on entry; may be null) is cleared when a
+// fused matrix is not unitary to 1e-10 (max |U^H U - I|).
 void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary,
                     cudaStream_t st);
 

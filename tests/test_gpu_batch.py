@@ -162,3 +162,31 @@ def test_batch_from_zero_ignores_prior_contents(sv, use_graph):
     finally:
         for s in states:
             s.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_tensor_core_sections(sv, use_graph):
+    """use_tc: sections with chunks of >= 11 bits run as fused tensor-core groups (per-row norm
+    restoration), smaller states stay on the SIMT groups, all in the same launch."""
+    ns, descs = _workload([8, 12, 14, 16, 11, 13, 17], 12, 0.02, 31, hea_n=15, hea_sets=2)
+    out, (items, sections, _) = _run_batch(sv, ns, descs, use_graph, repeats=2, chunk_bits=13, use_tc=1)
+    for n, d, got in zip(ns, descs, out):
+        assert_close(got, sim.simulate(n, d), "c64")
+
+
+def test_batch_tensor_core_multi_section_from_zero(sv):
+    ns, descs = _workload([18, 20, 15], 20, 1e-2, 41, hea_n=20, hea_sets=2)
+    gates = [sv.make_gates(d) for d in descs]
+    states = [sv.StateVector(n, "c64") for n in ns]
+    try:
+        b = sv.Batch(states, gates, chunk_bits=12, use_tc=1)
+        b.run(use_graph=True, from_zero=True)
+        b.synchronize()
+        b.close()
+        for n, d, s in zip(ns, descs, states):
+            got = s.get_state()
+            assert_close(got, sim.simulate(n, d), "c64")
+            assert abs(float(np.vdot(got.astype(np.complex128), got.astype(np.complex128)).real) - 1.0) < 1e-6
+    finally:
+        for s in states:
+            s.close()
