@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <thread>
 
 #include "sv_internal.h"
 
@@ -100,9 +102,20 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
     const bool want_tc = base.use_tc != 0;
     std::vector<ComposeSeg> compose;
     std::vector<DevGate<double>> compose_gates;
-    auto align = [&](size_t a) {
-        while (progs.size() % a) progs.push_back(0);
+    // per-state planning and program building, spread over host threads (each state into its own
+    // buffers, merged in state order below, so the result does not depend on the threading)
+    struct StateOut {
+        std::vector<BatchOp> ops;
+        std::vector<unsigned char> progs;
+        std::vector<ComposeSeg> cs;
+        std::vector<DevGate<double>> cg;
+        bool idle = false;
+        double bytes = 0;
+        bool failed = false;
+        sv_status code = SV_OK;
+        std::string msg;
     };
+    std::vector<StateOut> outs((size_t)count);
     for (int s = 0; s < count; ++s) {
         const sv_state *h = states[s];
         if (!h) fail(SV_ERR_ARG, "sv_batch_create: null state");
@@ -110,6 +123,12 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
         if (h->device != dev) fail(SV_ERR_ARG, "sv_batch_create: state on another device");
         if (h->n < 6) fail(SV_ERR_UNSUPPORTED, "sv_batch_create: states need at least 6 qubits");
         if (h->stream != b->stream) fail(SV_ERR_ARG, "sv_batch_create: all states must use one stream");
+    }
+    auto build_state = [&](int s, StateOut &out) {
+        auto align_out = [&](size_t al) {
+            while (out.progs.size() % al) out.progs.push_back(0);
+        };
+        const sv_state *h = states[s];
         sv_options o = base;
         o.chunk_bits = std::min(std::max(o.chunk_bits, 6), kBatchMaxChunkBits);
         o.gather_pinned = std::min(4, std::min(o.chunk_bits, h->n) - 2);
@@ -122,7 +141,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
         o.seg_bits = 4;
         o.use_tc = 0;  // the planner's own tensor-core rules do not apply to batch sections
         std::unique_ptr<sv_plan> plan(plan_blocking(h->n, gates[s], n_gates[s], o));
-        if (plan->ops.empty()) b->idle.emplace_back(h->amp, h->n);
+        if (plan->ops.empty()) out.idle = true;
         int opno = 0;
         for (const PlanOp &op : plan->ops) {
             if (op.gates.empty()) continue;
@@ -168,10 +187,10 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
             // operands and unitarity flags (tensor cores); the kernel runs the pieces one after
             // another on the resident chunk
             const bool tc = want_tc && k >= 11;
-            align(256);
+            align_out(256);
             BatchOp sec = bo;
             sec.op = opno++;
-            sec.prog_off = (uint32_t)progs.size();
+            sec.prog_off = (uint32_t)out.progs.size();
             sec.npiece = 0;
             sec.tc = tc ? 1 : 0;
             size_t p0 = 0;
@@ -211,41 +230,91 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                     d.g1 = (int16_t)dg.size();
                     ds.push_back(d);
                 }
-                const size_t at = progs.size();
-                progs.resize(at + 16, 0);
+                const size_t at = out.progs.size();
+                out.progs.resize(at + 16, 0);
                 const unsigned char *p = reinterpret_cast<const unsigned char *>(ds.data());
-                progs.insert(progs.end(), p, p + ds.size() * sizeof(DevSeg));
-                align(16);
+                out.progs.insert(out.progs.end(), p, p + ds.size() * sizeof(DevSeg));
+                align_out(16);
                 if (tc) {
                     for (size_t q = p0; q < p1; ++q) {  // B operands, written by the compose kernel
                         ComposeSeg cs{};
-                        cs.b_off = (uint32_t)progs.size();
+                        cs.b_off = (uint32_t)out.progs.size();
                         cs.flag_off = cs.b_off + TC_B_BYTES;
-                        cs.g0 = (int32_t)compose_gates.size();
+                        cs.g0 = (int32_t)out.cg.size();
                         for (int32_t gi : segs[q].gates) {
                             DevGate<double> g;
                             encode_gate<double>(gates[s][loc[gi].gi], loc[gi], segs[q], g);
-                            compose_gates.push_back(g);
+                            out.cg.push_back(g);
                         }
-                        cs.g1 = (int32_t)compose_gates.size();
-                        compose.push_back(cs);
-                        progs.resize(progs.size() + kBatchTcGroupBytes, 0);
+                        cs.g1 = (int32_t)out.cg.size();
+                        out.cs.push_back(cs);
+                        out.progs.resize(out.progs.size() + kBatchTcGroupBytes, 0);
                     }
                 } else {
                     p = reinterpret_cast<const unsigned char *>(dg.data());
-                    progs.insert(progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
+                    out.progs.insert(out.progs.end(), p, p + dg.size() * sizeof(DevGate<float>));
                 }
-                align(16);
-                const int32_t hd[4] = {(int32_t)ds.size(), (int32_t)dg.size(), (int32_t)(progs.size() - at), 0};
-                std::memcpy(progs.data() + at, hd, sizeof(hd));
+                align_out(16);
+                const int32_t hd[4] = {(int32_t)ds.size(), (int32_t)dg.size(), (int32_t)(out.progs.size() - at), 0};
+                std::memcpy(out.progs.data() + at, hd, sizeof(hd));
                 ++sec.npiece;
                 p0 = p1;
             }
-            sec.prog_bytes = (uint32_t)(progs.size() - sec.prog_off);
+            sec.prog_bytes = (uint32_t)(out.progs.size() - sec.prog_off);
             if (sec.npiece == 0) continue;
-            b->bytes += 2.0 * 8.0 * std::ldexp(1.0, n);
-            per_state[(size_t)s].push_back(sec);
+            out.bytes += 2.0 * 8.0 * std::ldexp(1.0, n);
+            out.ops.push_back(sec);
         }
+    
+    };
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nth = (int)std::max(1u, std::min(16u, std::min(hw ? hw : 1u, (unsigned)count)));
+        auto work = [&](int t) {
+            for (int s = t; s < count; s += nth) {
+                try {
+                    build_state(s, outs[(size_t)s]);
+                } catch (const Error &e) {
+                    outs[(size_t)s].failed = true;
+                    outs[(size_t)s].code = e.code;
+                    outs[(size_t)s].msg = e.msg;
+                } catch (const std::bad_alloc &) {
+                    outs[(size_t)s].failed = true;
+                    outs[(size_t)s].code = SV_ERR_OOM;
+                    outs[(size_t)s].msg = "host allocation failed";
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (std::thread &th : pool) th.join();
+    }
+    // merge in state order
+    auto align = [&](size_t al) {
+        while (progs.size() % al) progs.push_back(0);
+    };
+    for (int s = 0; s < count; ++s) {
+        StateOut &out = outs[(size_t)s];
+        if (out.failed) fail(out.code, out.msg);
+        if (out.idle) b->idle.emplace_back(states[s]->amp, states[s]->n);
+        b->bytes += out.bytes;
+        align(256);
+        const uint32_t base_off = (uint32_t)progs.size();
+        const int32_t gate_base = (int32_t)compose_gates.size();
+        progs.insert(progs.end(), out.progs.begin(), out.progs.end());
+        for (BatchOp &o : out.ops) {
+            o.prog_off += base_off;
+            per_state[(size_t)s].push_back(o);
+        }
+        for (ComposeSeg cs : out.cs) {
+            cs.b_off += base_off;
+            cs.flag_off += base_off;
+            cs.g0 += gate_base;
+            cs.g1 += gate_base;
+            compose.push_back(cs);
+        }
+        compose_gates.insert(compose_gates.end(), out.cg.begin(), out.cg.end());
     }
     // queue order: section level by section level, round-robin over the states
     std::vector<BatchOp> ops;
