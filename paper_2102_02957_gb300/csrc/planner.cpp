@@ -326,9 +326,11 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
 // ---------------------------------------------------------------------------------------
 // Register groups.  Inside a blocking section each chunk lives in shared memory; a group is
 // a set of r chunk bits whose 2^r amplitudes one thread holds in registers while it applies
-// every gate of the group.  Gates are taken greedily in section order; a gate that does not
-// fit is deferred and blocks its bits for the rest of the group (so per-qubit gate order is
-// kept), the same rule the transpiler uses one level up.
+// every gate of the group.  The group's bits start from the first pending gate's and grow by
+// look-ahead (the pending gate whose new bits let the group take the most gates); the group then
+// takes, in section order, every gate inside its bits, and a gate that is not taken blocks its
+// bits for the rest of the group (so per-qubit gate order is kept) -- the transpiler's
+// QB_BLOCKED rule one level down.
 //
 // Lane layout: the lanes that share a shared-memory wavefront (16 for 8-byte amplitudes, 8 for
 // 16-byte ones) must enumerate distinct bank slots.  A chunk bit k contributes the slot vector
@@ -346,16 +348,46 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
         return mk;
     };
     const int rr = std::min(r, width);
+    // gates a group on `bits` takes: in order, those inside `bits` and not behind a deferred gate
+    auto takes = [&](uint64_t bits) {
+        uint64_t blocked = 0;
+        int k = 0;
+        for (int32_t idx : pending) {
+            const uint64_t mk = mask_of(gates[idx]);
+            if ((mk & ~bits) == 0 && (mk & blocked) == 0) ++k;
+            else blocked |= mk;
+        }
+        return k;
+    };
     std::vector<int32_t> rest;
     while (!pending.empty()) {
-        uint64_t set = 0, blocked = 0;
+        // the group's bits: the first pending gate's, then, one pending gate at a time (the first
+        // 64 with new bits), those that let the group take the most gates
+        uint64_t set = mask_of(gates[pending.front()]);
+        while (popc(set) < rr) {
+            uint64_t best = 0;
+            int best_k = -1;
+            size_t tried = 0;
+            for (size_t i = 0; i < pending.size() && tried < 64; ++i) {
+                const uint64_t fresh = mask_of(gates[pending[i]]) & ~set;
+                if (!fresh || popc(set | fresh) > rr) continue;
+                ++tried;
+                const int k = takes(set | fresh);
+                if (k > best_k) {
+                    best_k = k;
+                    best = fresh;
+                }
+            }
+            if (!best) break;
+            set |= best;
+        }
+        uint64_t blocked = 0;
         HostSeg s;
         s.r = rr;
         rest.clear();
         for (int32_t idx : pending) {
             const uint64_t mk = mask_of(gates[idx]);
-            if ((mk & blocked) == 0 && popc(set | mk) <= rr) {
-                set |= mk;
+            if ((mk & ~set) == 0 && (mk & blocked) == 0) {
                 s.gates.push_back(idx);
             } else {
                 blocked |= mk;
