@@ -216,8 +216,9 @@ sv_status sv_batch_tune(int32_t count, const sv_handle *states, const sv_gate *c
 
 /* ------------------------------------------------------------------ autotuning */
 /* Time candidate executions of this circuit on a scratch n-qubit state of `dtype` (chunk bits
- * 11..13, register-group width 4/5, gathered or chunk_swap layout, tensor cores on/off for
- * complex64) and write the fastest options to *best (its other fields are copied from *base).
+ * 11..13, register-group width 4/5, gathered or chunk_swap layout, the paper's or the look-ahead
+ * chunk choice, tensor cores on/off for complex64) and write the fastest options to *best (its
+ * other fields are copied from *base).
  * best_ms receives the measured milliseconds of one application with those options.  Allocates
  * and frees its own scratch state; synchronises the device. */
 sv_status sv_autotune(int32_t n, int32_t dtype, const sv_gate *gates, int64_t n_gates, const sv_options *base,

@@ -498,15 +498,18 @@ sv_status sv_autotune(int32_t n, int32_t dtype, const sv_gate *gates, int64_t n_
         for (int c = std::max(std::min(n, 11), std::min(cmax, 6)); c <= cmax; ++c)
             for (int seg : {4, 5})
                 for (int pin : {0, 4})
-                    for (int tc : {0, 1}) {
+                    for (int tc : {0, 1})
+                        for (int la : {0, 1}) {
                         if (dtype != SV_C64 && (seg == 5 || tc)) continue;
                         if (tc && seg != 4) continue;
                         if (pin && c - pin < 2) continue;
+                        if (la && !pin) continue;  // look-ahead chunk choice: gathered chunks only
                         sv_options o = b0;
                         o.chunk_bits = c;
                         o.seg_bits = seg;
                         o.gather_pinned = pin;
                         o.use_tc = tc;
+                        o.lookahead = la;
                         sv_plan_h p = nullptr;
                         if (sv_plan_blocking(n, gates, n_gates, &o, &p) != SV_OK) continue;
                         double ms = 1e300;
