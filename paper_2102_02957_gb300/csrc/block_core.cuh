@@ -382,7 +382,7 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // register groups: every thread writes its group's 32 reals split into TF32 high and low parts
 // to its TMEM lane (A_hi, A_lo), one thread issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo
 // (3 x 4 MMAs, M = 128, N = K = 32, FP32 accumulation), and every thread reads its row of D back.
-// Two tiles are in flight per group; TMEM columns of tile buffer k: A_hi [tcol + 96k, +32),
+// NB (1 or 2) tiles are in flight per group; TMEM columns of tile buffer k: A_hi [tcol + 96k, +32),
 // A_lo [+32, +64), D [+64, +96); `mbar[k]` signals its MMAs' completion.
 //
 // RENORM: the tensor cores' FP32 accumulation truncates, shrinking each result by a few units
@@ -390,7 +390,7 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // per circuit set RENORM: for a group whose fused matrix is unitary (the int after B_lo is
 // nonzero) each output row is rescaled to its input row's norm, as y <- y (1 + d) with
 // d = (|x|^2 - |y|^2) / (2 |y|^2) (a scale factor rounded next to 1 would itself be biased).
-template <int NC, bool RENORM = false>
+template <int NC, bool RENORM = false, int NB = 2>
 __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint32_t bhi, int ctid, const int *swz,
                                                int c, uint32_t tcol, int bar_id, uint64_t *mbar, uint32_t (&phase)[2],
                                                volatile int *abort_flag) {
@@ -517,17 +517,24 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
     int pb, ps;
     float pn;
-    if (!stage(0, 0, pb, ps, pn)) return false;
-    for (int t = 1; t < T; ++t) {
-        int nb, ns;
-        float nn;
-        if (!stage(t, t & 1, nb, ns, nn)) return false;
-        finish((t - 1) & 1, pb, ps, pn);
-        pb = nb;
-        ps = ns;
-        pn = nn;
+    if constexpr (NB == 2) {
+        if (!stage(0, 0, pb, ps, pn)) return false;
+        for (int t = 1; t < T; ++t) {
+            int nb, ns;
+            float nn;
+            if (!stage(t, t & 1, nb, ns, nn)) return false;
+            finish((t - 1) & 1, pb, ps, pn);
+            pb = nb;
+            ps = ns;
+            pn = nn;
+        }
+        finish((T - 1) & 1, pb, ps, pn);
+    } else {  // one tile buffer: tiles one after another
+        for (int t = 0; t < T; ++t) {
+            if (!stage(t, 0, pb, ps, pn)) return false;
+            finish(0, pb, ps, pn);
+        }
     }
-    finish((T - 1) & 1, pb, ps, pn);
     return !ptx::named_bar_or(bar_id, NC, failed);  // the group leaves together
 }
 

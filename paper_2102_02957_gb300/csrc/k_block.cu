@@ -133,10 +133,12 @@ __device__ __forceinline__ void store_chunk(T2 *state, int c, int64_t j, const T
     ptx::mbar_arrive(empty_slot);
 }
 
-constexpr int CG = 2;  // consumer groups per CTA
+constexpr int CG2 = 2;  // consumer groups per CTA (default)
 
-template <typename T, int R, int NC, int KU, bool TC>
-__global__ void __launch_bounds__(CG * NC + 32, 1)
+// G consumer groups per CTA; tensor-core groups keep NB tile buffers each (G * NB * 96 <= 512
+// TMEM columns).
+template <typename T, int R, int NC, int KU, bool TC, int G = CG2, int NB = 2>
+__global__ void __launch_bounds__(G * NC + 32, 1)
     k_block(typename V2<T>::type *__restrict__ state, int c, int64_t nchunks, int nbuf,
             const unsigned char *__restrict__ prog, int nseg, int ngate, int *err,
             const __grid_constant__ CUtensorMap tmap, const GatherArgs ga_in) {
@@ -157,8 +159,8 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(sprog + ((prog_bytes + 15) & ~15));
     uint64_t *empty = full + nbuf;
     uint64_t *mma_bar = empty + nbuf;  // two per consumer group (tensor-core path)
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(mma_bar + 2 * CG);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 2 * CG) + 1;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(mma_bar + 2 * G);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 2 * G) + 1;
     __shared__ int swz[24];
     constexpr uint32_t kTmemCols = 512;  // 2 tiles x 96 columns per consumer group
 
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
-        for (int g = 0; g < 2 * CG; ++g) ptx::mbar_init(&mma_bar[g], 1);
+        for (int g = 0; g < 2 * G; ++g) ptx::mbar_init(&mma_bar[g], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -193,14 +195,14 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     }
 
     // -------------------------------------------------------------- consumers
-    // CG groups of NC threads take alternate chunks, so one group's shared-memory phases
+    // G groups of NC threads take alternate chunks, so one group's shared-memory phases
     // overlap another group's arithmetic; each group synchronises on its own named barrier.
     const int cg = (threadIdx.x - 32) / NC;
     const int ctid = (threadIdx.x - 32) % NC;
     const int bar_id = 1 + cg;
     uint32_t mma_phase[2] = {0, 0};
     bool failed = false;
-    for (int64_t it = cg; it < count; it += CG) {
+    for (int64_t it = cg; it < count; it += G) {
         const int s = (int)(it % nbuf);
         const int64_t j = blockIdx.x + it * gridDim.x;
         if (!ptx::mbar_wait(&full[s], (uint32_t)((it / nbuf) & 1), kWaitLimitNs)) {
@@ -215,9 +217,9 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
         for (int si = 0; si < nseg; ++si) {
             const uint32_t seg_addr = ptx::smem_addr(segs) + (uint32_t)(si * sizeof(DevSeg));
             if constexpr (TC) {
-                if (!run_segment_tc<NC>(ptx::smem_addr(buf), seg_addr,
+                if (!run_segment_tc<NC, false, NB>(ptx::smem_addr(buf), seg_addr,
                                         ptx::smem_addr(sprog + seg_bytes) + (uint32_t)(si * TC_B_BYTES), ctid, swz, c,
-                                        tmem_base + (uint32_t)(cg * 192), bar_id, &mma_bar[2 * cg], mma_phase,
+                                        tmem_base + (uint32_t)(cg * NB * 96), bar_id, &mma_bar[2 * cg], mma_phase,
                                         abort_flag)) {
                     failed = true;
                     break;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     if constexpr (TC) {
         // every consumer is done with tensor memory before the allocating warp frees it
         ptx::tc_fence_before();
-        ptx::named_bar_sync(1 + CG, CG * NC);
+        ptx::named_bar_sync(1 + G, G * NC);
         if ((threadIdx.x >> 5) == 1) {
             ptx::tc_fence_after();
             ptx::tmem_dealloc(tmem_base, kTmemCols);
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(CG * NC + 32, 1)
     }
 }
 
-template <typename T, int R, int NC, int KU, bool TC = false>
+template <typename T, int R, int NC, int KU, bool TC = false, int G = CG2, int NB = 2>
 void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ngate, int *err, cudaStream_t st,
                   const CUtensorMap &tmap, const GatherArgs &ga) {
     if (ce - R - 5 > kMaxRest) fail(SV_ERR_UNSUPPORTED, "chunk too wide for the register-group layout");
@@ -259,7 +261,7 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     const size_t prog_bytes =
         (seg_bytes + (TC ? (size_t)nseg * TC_B_BYTES : ngate * sizeof(DevGate<T>)) + 15) & ~size_t(15);
     const size_t extra = prog_bytes + 256;  // program + mbarriers, abort flag, TMEM address
-    int nbuf = 3;
+    int nbuf = TC ? G + 2 : 3;  // tensor cores: every consumer group holds a chunk, plus prefetch
     const size_t max_smem = 227 * 1024 - 1024;  // minus the static swizzle table (1 KiB aligned)
     while (nbuf > 1 && nbuf * chunk_bytes + extra > max_smem) --nbuf;
     size_t smem = nbuf * chunk_bytes + extra;
@@ -267,15 +269,15 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     // a tensor-core CTA takes all of its SM's tensor memory: reserve over half the shared memory
     // so that the scheduler never places two on one SM
     if (TC && smem < 120 * 1024) smem = 120 * 1024;
-    auto kern = k_block<T, R, NC, KU, TC>;
+    auto kern = k_block<T, R, NC, KU, TC, G, NB>;
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(block)");
     int per_sm = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CG * NC + 32, smem), "occupancy(block)");
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * NC + 32, smem), "occupancy(block)");
     if (per_sm < 1) per_sm = 1;
     if (TC) per_sm = 1;  // each CTA allocates all 512 tensor-memory columns of its SM
     const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm);
-    kern<<<(unsigned)grid, CG * NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
+    kern<<<(unsigned)grid, G * NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
                                                 ngate, err, tmap, ga);
     check_cuda(cudaGetLastError(), "block kernel launch");
 }
@@ -389,7 +391,12 @@ void launch_block_tc(void *state, int n, int c, const GatherLayout *lay, const v
         m = make_gather_map(state, n, *lay, 8);
         ga = lay->args;
     }
-    launch_typed<float, 4, 128, 1, true>(state, n, ce, dev_prog, nseg, 0, dev_err, st, m, ga);
+    // four consumer groups with one tile buffer each where the chunks are small enough: more
+    // warps per SM in the same 512 TMEM columns
+    if (ce <= 12)
+        launch_typed<float, 4, 128, 1, true, 4, 1>(state, n, ce, dev_prog, nseg, 0, dev_err, st, m, ga);
+    else
+        launch_typed<float, 4, 128, 1, true>(state, n, ce, dev_prog, nseg, 0, dev_err, st, m, ga);
 }
 
 }  // namespace sv

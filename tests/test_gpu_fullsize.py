@@ -1,9 +1,9 @@
 """Parity at the benchmark's full sizes, in the launch configurations the benchmark times.
 
-* quantum volume, n = 30, depth 30, complex64 (8 GiB), chunk 13, gathered chunks with 4 pinned
+* quantum volume, n = 30, depth 30, complex64 (8 GiB), chunk 12, gathered chunks with 4 pinned
   bits, on the tensor-core and on the SIMT register-group paths: every amplitude against the
   oracle's complex128 simulation (16 GiB on the host; about two minutes of host cores);
-* the same circuit followed by its inverse returns |0..0> (tensor-core path);
+* the same circuit followed by its inverse returns |0..0> (tensor-core path, chunk 13);
 * QFT of a seeded basis state, n = 28, complex128 (4 GiB), chunk 12 with the paper's chunk_swap
   layout and the final reordering: every amplitude against the closed form;
 * random-layer circuit, n = 28, depth 40, complex128: the cache-blocked path (chunk 12) against

@@ -266,7 +266,7 @@ def test_chunk_larger_than_shared_memory_rejected(sv):
 
 # ------------------------------------------------------------------ tensor-core fused groups (3xTF32)
 
-@pytest.mark.parametrize("n,c,pinned", [(14, 11, 0), (16, 12, 0), (17, 13, 0), (16, 11, 4), (20, 13, 4), (13, 13, 0)])
+@pytest.mark.parametrize("n,c,pinned", [(14, 11, 0), (16, 12, 0), (17, 13, 0), (16, 11, 4), (20, 12, 4), (20, 13, 4), (13, 13, 0), (12, 12, 0)])
 def test_tensor_core_fused_groups(sv, n, c, pinned):
     desc = _mixed(n, 150, 500 + n + c) + cg.quantum_volume(n, 6, n + 2) + cg.qft(n)
     ref = sim.simulate(n, desc, 9)
@@ -284,11 +284,13 @@ def test_tensor_core_many_groups_per_section(sv):
     assert_close(got, ref, "c64")
 
 
-def test_tensor_core_quantum_volume_24(sv):
+@pytest.mark.parametrize("c", [12, 13])
+def test_tensor_core_quantum_volume_24(sv, c):
+    # 12-bit chunks run four single-buffered consumer groups, 13-bit ones two double-buffered
     n = 24
     desc = cg.quantum_volume(n, 10, 19)
     ref = sim.simulate(n, desc)
-    got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=13, gather_pinned=4, use_tc=1))
+    got = _run(sv, n, desc, "c64", plan_opts=dict(chunk_bits=c, gather_pinned=4, use_tc=1))
     assert_close(got, ref, "c64")
 
 
