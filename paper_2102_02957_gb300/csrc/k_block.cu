@@ -11,8 +11,9 @@
 //  * warp 0, lane 0 is the producer (produce_chunks): it streams the CTA's chunks
 //    j = blockIdx.x + t*gridDim.x into a ring of shared-memory buffers with bulk or tensor
 //    asynchronous copies (TMA engine) completing on "full" mbarriers;
-//  * two consumer groups of NC threads take alternate chunks, so one group's shared-memory and
-//    barrier phases overlap the other's arithmetic.  For each chunk a group runs the section's
+//  * G consumer groups of NC threads (two; four for tensor-core sections of chunks up to 12 bits)
+//    take chunks in turn, so one group's shared-memory and barrier phases overlap another's
+//    arithmetic.  For each chunk a group runs the section's
 //    register groups -- SIMT (run_segment: each thread loads the 2^R amplitudes spanned by the
 //    group's R chunk bits into registers, applies every gate of the group there, stores them
 //    back) or tensor cores (run_segment_tc: the group's fused unitary applied to 128-row tiles
@@ -202,10 +203,19 @@ __global__ void __launch_bounds__(G * NC + 32, 1)
     const int bar_id = 1 + cg;
     uint32_t mma_phase[2] = {0, 0};
     bool failed = false;
-    for (int64_t it = cg; it < count; it += G) {
+    // A parity wait cannot tell this chunk's load (use u = it / nbuf of slot s) from the slot's
+    // previous, still incomplete one (another group's chunk it - nbuf).  So a group first waits
+    // for that previous chunk's write-back (empty[s], use u - 1), which follows its load: then
+    // full[s] is at use u.  That wait is itself unambiguous: use u - 2 of empty[s] was observed
+    // by the producer before it issued this group's previous chunk.  The argument needs every
+    // group's previous chunk to be at most nbuf back, so at most nbuf groups take chunks.
+    const int geff = G < nbuf ? G : nbuf;
+    for (int64_t it = cg; cg < geff && it < count; it += geff) {
         const int s = (int)(it % nbuf);
+        const int64_t u = it / nbuf;
         const int64_t j = blockIdx.x + it * gridDim.x;
-        if (!ptx::mbar_wait(&full[s], (uint32_t)((it / nbuf) & 1), kWaitLimitNs)) {
+        if ((u > 0 && !ptx::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), kWaitLimitNs)) ||
+            !ptx::mbar_wait(&full[s], (uint32_t)(u & 1), kWaitLimitNs)) {
             atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
             *abort_flag = 1;
         }

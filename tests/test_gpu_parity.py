@@ -88,6 +88,18 @@ def test_blocked_mixed(sv, dtype, n, c, reserve):
     assert_close(_run(sv, n, desc, dtype, basis=3, plan_opts=dict(chunk_bits=c, reserve=reserve)), ref, dtype)
 
 
+@pytest.mark.parametrize("dtype,n,c,pinned", [("c128", 22, 13, 0), ("c64", 22, 14, 0), ("c128", 22, 13, 4),
+                                              ("c64", 23, 13, 0)])
+def test_blocked_wide_chunks_many_per_block(sv, dtype, n, c, pinned):
+    """Chunks so wide that fewer shared-memory buffers than consumer groups fit (128 KiB chunks:
+    one buffer) or only one spare (64 KiB), with hundreds of chunks, so every thread block works
+    through several of them: the buffer hand-over between consumer groups is exercised."""
+    desc = cg.random_layers(n, 6, 900 + c) + cg.quantum_volume(n, 2, 901)
+    ref = sim.simulate(n, desc, 5)
+    got = _run(sv, n, desc, dtype, basis=5, plan_opts=dict(chunk_bits=c, gather_pinned=pinned))
+    assert_close(got, ref, dtype)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n,c", [(12, 6), (16, 10)])
 def test_blocked_keep_layout(sv, dtype, n, c):
