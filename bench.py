@@ -234,7 +234,7 @@ def run_reference_batch(args):
 
 def _config(w):
     return {"workload": f"{args_workload_name(w)}", "n": w["n"], "gates": len(w["desc"]), "chunk_bits": w["c"],
-            "state": "complex64", "l2": "state 8 GiB >> 129 MB L2 (no flush needed)"}
+            "gather_pinned": w.get("pinned"), "state": "complex64", "l2": "state 8 GiB >> 129 MB L2 (no flush needed)"}
 
 
 def args_workload_name(w):
@@ -539,7 +539,9 @@ def run_ours(args):
         w["c"] = args.chunk_bits
     n, c, desc = w["n"], w["c"], w["desc"]
     G = len(desc)
-    plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=args.gather_pinned, use_tc=int(args.tc))
+    pinned = args.gather_pinned if args.gather_pinned >= 0 else w.get("pinned", 4)
+    w["pinned"] = pinned
+    plan_opts = dict(chunk_bits=c, seg_bits=args.seg_bits, gather_pinned=pinned, use_tc=int(args.tc))
     stream = torch.cuda.Stream()
     st = sv.StateVector(n, "c64", stream=stream)
     sweep_bytes = 2.0 * (1 << n) * 8
@@ -715,8 +717,9 @@ def main():
     ap.add_argument("--tc", type=int, default=1, help="1: fused register groups on the tensor cores (3xTF32)")
     ap.add_argument("--batch-tc", type=int, default=1,
                     help="batched workloads: 1 runs sections of >= 11 chunk bits on the tensor cores (128-thread CTAs)")
-    ap.add_argument("--gather-pinned", type=int, default=4,
-                    help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low bits")
+    ap.add_argument("--gather-pinned", type=int, default=-1,
+                    help="0: chunk_swap passes (the paper's layout moves); p > 0: gathered chunks with p pinned low "
+                         "bits; default: the workload's (5 for quantum volume: 256-byte tensor-copy boxes)")
     ap.add_argument("--planner", default="lookahead", choices=["rule", "lookahead", "steered"],
                     help="rule: the paper's chunk choice; lookahead: the chunk that takes the most gates; "
                          "steered: the learned cost model picks among both and smaller chunks (trained before timing)")

@@ -186,10 +186,10 @@ WORKLOADS = {
     "rl16": dict(kind="random_layers", n=16, depth=20, seed=1, c=10),
     "qft28": dict(kind="qft", n=28, seed=2, c=12),
     "rl28": dict(kind="random_layers", n=28, depth=40, seed=3, c=12),
-    "qv30": dict(kind="quantum_volume", n=30, depth=30, seed=4, c=12),
-    "qv26": dict(kind="quantum_volume", n=26, depth=10, seed=4, c=12),
+    "qv30": dict(kind="quantum_volume", n=30, depth=30, seed=4, c=12, pinned=5),
+    "qv26": dict(kind="quantum_volume", n=26, depth=10, seed=4, c=12, pinned=5),
     "rl32": dict(kind="random_layers", n=32, depth=32, seed=7, c=13),
-    "qv32": dict(kind="quantum_volume", n=32, depth=32, seed=7, c=12),
+    "qv32": dict(kind="quantum_volume", n=32, depth=32, seed=7, c=12, pinned=5),
 }
 
 

@@ -17,8 +17,9 @@
 //    register groups -- SIMT (run_segment: each thread loads the 2^R amplitudes spanned by the
 //    group's R chunk bits into registers, applies every gate of the group there, stores them
 //    back) or tensor cores (run_segment_tc: the group's fused unitary applied to 128-row tiles
-//    with tcgen05 MMAs) -- then one consumer writes the chunk back (store_chunk) and releases the
-//    buffer to the producer through an "empty" mbarrier once the write-back has read it.
+//    with tcgen05 MMAs) -- then hand it to the store thread through a "done" mbarrier;
+//  * warp 1, lane 0 is the store thread (store_chunks): it writes the chunks back in order and
+//    releases each buffer to the producer through an "empty" mbarrier once the copy has read it.
 //
 // Shared-memory layout of a chunk while it is being worked on: amplitude i sits in slot
 // i ^ F(i), where F XORs a fixed non-zero pattern V[k] into the low slot bits for every set
@@ -109,10 +110,10 @@ __device__ __forceinline__ void produce_chunks(T2 *state, int c, int64_t count, 
         (void)ptx::mbar_wait(&full[it % nbuf], (uint32_t)((it / nbuf) & 1), kWaitLimitNs);
 }
 
-// Write chunk j back from shared memory (one thread) and release its slot once read.
+// Issue the copies that write chunk j back from shared memory (one thread).
 template <typename T2>
-__device__ __forceinline__ void store_chunk(T2 *state, int c, int64_t j, const T2 *buf, uint64_t *empty_slot,
-                                            const GatherArgs &ga, const CUtensorMap *tmap) {
+__device__ __forceinline__ void write_chunk(T2 *state, int c, int64_t j, const T2 *buf, const GatherArgs &ga,
+                                            const CUtensorMap *tmap) {
     const int chunk_amps = 1 << c;
     const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
     const unsigned char *srcs = reinterpret_cast<const unsigned char *>(buf);
@@ -129,9 +130,30 @@ __device__ __forceinline__ void store_chunk(T2 *state, int c, int64_t j, const T
             ptx::bulk_s2g(dstg + o, srcs + o, b);
         }
     }
-    ptx::bulk_commit();
-    ptx::bulk_wait_read<0>();
-    ptx::mbar_arrive(empty_slot);
+}
+
+// Store thread: write the CTA's chunks back in order as their consumer groups finish them
+// (done[slot]) and release each slot to the producer (empty[slot]) once the copy has read it,
+// so that a consumer group goes on to its next chunk without waiting for its write-back.
+template <typename T2>
+__device__ __forceinline__ void store_chunks(T2 *state, int c, int64_t count, int nbuf, const T2 *bufs, uint64_t *done,
+                                             uint64_t *empty, volatile int *abort_flag, int *err,
+                                             const GatherArgs &ga, const CUtensorMap *tmap) {
+    const int chunk_amps = 1 << c;
+    for (int64_t it = 0; it < count; ++it) {
+        const int s = (int)(it % nbuf);
+        // use it / nbuf of done[s]: the previous use (chunk it - nbuf) was waited for here
+        if (!ptx::mbar_wait(&done[s], (uint32_t)((it / nbuf) & 1), kWaitLimitNs) || *abort_flag) {
+            atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+        }
+        write_chunk<T2>(state, c, blockIdx.x + it * gridDim.x, bufs + (size_t)s * chunk_amps, ga, tmap);
+        ptx::bulk_commit();
+        ptx::bulk_wait_read<0>();
+        ptx::mbar_arrive(&empty[s]);
+    }
+    ptx::bulk_wait<0>();
 }
 
 constexpr int CG2 = 2;  // consumer groups per CTA (default)
@@ -139,7 +161,7 @@ constexpr int CG2 = 2;  // consumer groups per CTA (default)
 // G consumer groups per CTA; tensor-core groups keep NB tile buffers each (G * NB * 96 <= 512
 // TMEM columns).
 template <typename T, int R, int NC, int KU, bool TC, int G = CG2, int NB = 2>
-__global__ void __launch_bounds__(G * NC + 32, 1)
+__global__ void __launch_bounds__(G * NC + 64, 1)
     k_block(typename V2<T>::type *__restrict__ state, int c, int64_t nchunks, int nbuf,
             const unsigned char *__restrict__ prog, int nseg, int ngate, int *err,
             const __grid_constant__ CUtensorMap tmap, const GatherArgs ga_in) {
@@ -159,7 +181,8 @@ __global__ void __launch_bounds__(G * NC + 32, 1)
     const DevGate<T> *gates = reinterpret_cast<const DevGate<T> *>(sprog + seg_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(sprog + ((prog_bytes + 15) & ~15));
     uint64_t *empty = full + nbuf;
-    uint64_t *mma_bar = empty + nbuf;  // two per consumer group (tensor-core path)
+    uint64_t *done = empty + nbuf;
+    uint64_t *mma_bar = done + nbuf;  // two per consumer group (tensor-core path)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(mma_bar + 2 * G);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_bar + 2 * G) + 1;
     __shared__ int swz[24];
@@ -172,12 +195,13 @@ __global__ void __launch_bounds__(G * NC + 32, 1)
         for (int s = 0; s < nbuf; ++s) {
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&done[s], 1);
         }
         for (int g = 0; g < 2 * G; ++g) ptx::mbar_init(&mma_bar[g], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (TC && (threadIdx.x >> 5) == 1) ptx::tmem_alloc(ptx::smem_addr(tmem_slot), kTmemCols);
+    if (TC && (threadIdx.x >> 5) == 2) ptx::tmem_alloc(ptx::smem_addr(tmem_slot), kTmemCols);
     if (TC) {
         ptx::fence_proxy_async_smem();  // B operands written by generic stores, read by the tensor cores
         ptx::tc_fence_before();
@@ -188,18 +212,20 @@ __global__ void __launch_bounds__(G * NC + 32, 1)
 
     const int64_t count = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    if (threadIdx.x < 32) {
-        // ------------------------------------------------------------ producer
+    if (threadIdx.x < 64) {
+        // ------------------------------------------------- producer (warp 0), store (warp 1)
         if (threadIdx.x == 0)
             produce_chunks<T2>(state, c, count, nbuf, bufs, full, empty, abort_flag, err, ga, &tmap);
+        else if (threadIdx.x == 32)
+            store_chunks<T2>(state, c, count, nbuf, bufs, done, empty, abort_flag, err, ga, &tmap);
         return;
     }
 
     // -------------------------------------------------------------- consumers
     // G groups of NC threads take alternate chunks, so one group's shared-memory phases
     // overlap another group's arithmetic; each group synchronises on its own named barrier.
-    const int cg = (threadIdx.x - 32) / NC;
-    const int ctid = (threadIdx.x - 32) % NC;
+    const int cg = (threadIdx.x - 64) / NC;
+    const int ctid = (threadIdx.x - 64) % NC;
     const int bar_id = 1 + cg;
     uint32_t mma_phase[2] = {0, 0};
     bool failed = false;
@@ -245,15 +271,14 @@ __global__ void __launch_bounds__(G * NC + 32, 1)
             break;
         }
         if (nseg == 0) ptx::fence_proxy_async_smem();
-        // release the buffer to the producer once the write-back has read it
-        if (ctid == 0) store_chunk<T2>(state, c, j, buf, &empty[s], ga, &tmap);
+        // hand the chunk to the store thread (the group's last barrier ordered all its writes)
+        if (ctid == 0) ptx::mbar_arrive(&done[s]);
     }
-    if (ctid == 0) ptx::bulk_wait<0>();
     if constexpr (TC) {
         // every consumer is done with tensor memory before the allocating warp frees it
         ptx::tc_fence_before();
         ptx::named_bar_sync(1 + G, G * NC);
-        if ((threadIdx.x >> 5) == 1) {
+        if ((threadIdx.x >> 5) == 2) {
             ptx::tc_fence_after();
             ptx::tmem_dealloc(tmem_base, kTmemCols);
         }
@@ -270,8 +295,10 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     const size_t seg_bytes = (nseg * sizeof(DevSeg) + 15) & ~size_t(15);
     const size_t prog_bytes =
         (seg_bytes + (TC ? (size_t)nseg * TC_B_BYTES : ngate * sizeof(DevGate<T>)) + 15) & ~size_t(15);
-    const size_t extra = prog_bytes + 256;  // program + mbarriers, abort flag, TMEM address
     int nbuf = TC ? G + 2 : 3;  // tensor cores: every consumer group holds a chunk, plus prefetch
+    // program + mbarriers (full, empty, done per buffer; two per consumer group), abort flag,
+    // TMEM address
+    const size_t extra = prog_bytes + (size_t)(3 * nbuf + 2 * G) * 8 + 16;
     const size_t max_smem = 227 * 1024 - 1024;  // minus the static swizzle table (1 KiB aligned)
     while (nbuf > 1 && nbuf * chunk_bytes + extra > max_smem) --nbuf;
     size_t smem = nbuf * chunk_bytes + extra;
@@ -283,11 +310,11 @@ void launch_typed(void *state, int n, int ce, const void *prog, int nseg, int ng
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(block)");
     int per_sm = 0;
-    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * NC + 32, smem), "occupancy(block)");
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * NC + 64, smem), "occupancy(block)");
     if (per_sm < 1) per_sm = 1;
     if (TC) per_sm = 1;  // each CTA allocates all 512 tensor-memory columns of its SM
     const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms() * per_sm);
-    kern<<<(unsigned)grid, G * NC + 32, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
+    kern<<<(unsigned)grid, G * NC + 64, smem, st>>>((T2 *)state, ce, nchunks, nbuf, (const unsigned char *)prog, nseg,
                                                 ngate, err, tmap, ga);
     check_cuda(cudaGetLastError(), "block kernel launch");
 }

@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configurations the benchmark times.
 
-* quantum volume, n = 30, depth 30, complex64 (8 GiB), chunk 12, gathered chunks with 4 pinned
+* quantum volume, n = 30, depth 30, complex64 (8 GiB), chunk 12, gathered chunks with 5 pinned
   bits, on the tensor-core and on the SIMT register-group paths: every amplitude against the
   oracle's complex128 simulation (16 GiB on the host; about two minutes of host cores);
 * the same circuit followed by its inverse returns |0..0> (tensor-core path, chunk 13);
@@ -57,7 +57,8 @@ def _run(sv, n, desc, dtype, basis=0, **plan_opts):
 @pytest.mark.parametrize("use_tc", [1, 0])
 def test_quantum_volume_30_bench_config_vs_oracle(sv, qv30_oracle, use_tc):
     w = cg.WORKLOADS["qv30"]
-    got = _run(sv, 30, cg.build("qv30"), "c64", chunk_bits=w["c"], gather_pinned=4, use_tc=use_tc, seg_bits=4)
+    got = _run(sv, 30, cg.build("qv30"), "c64", chunk_bits=w["c"], gather_pinned=w["pinned"], use_tc=use_tc,
+               seg_bits=4, lookahead=1)
     mx, inf = assert_close(got, qv30_oracle, "c64")
     print(f"qv30 use_tc={use_tc}: max-abs {mx:.3e}, 1-F {inf:.3e}")
 
