@@ -18,6 +18,12 @@ template <> struct V2<double> { using type = double2; };
 __constant__ int c_swz64[24] = {SV_SWZ64_LIST};
 __constant__ int c_swz128[24] = {SV_SWZ128_LIST};
 
+// Lowest set bit of a non-zero loop index that unrolling makes a constant.  Indexing a step table
+// with __ffs(b) - 1 is not folded and puts the table in local memory; this expression is.
+__host__ __device__ constexpr int low_bit(int b) {
+    return (b & 1) ? 0 : (b & 2) ? 1 : (b & 4) ? 2 : (b & 8) ? 3 : 4;
+}
+
 __device__ __forceinline__ int insert0(int x, int p) { return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1)); }
 
 template <typename T>
@@ -452,7 +458,7 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
 #pragma unroll
         for (int b = 0; b < NA; ++b) {
-            if (b) off ^= ld_step[__ffs(b) - 1];
+            if (b) off ^= ld_step[low_bit(b)];
             const int gidx = b ^ (b >> 1);  // Gray code: this amplitude's local index
             float xr, xi;
             SM<float>::ld(buf + off, xr, xi);
@@ -509,7 +515,7 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
 #pragma unroll
         for (int b = 0; b < NA; ++b) {
-            if (b) off ^= st_step[__ffs(b) - 1];
+            if (b) off ^= st_step[low_bit(b)];
             const int gidx = b ^ (b >> 1);
             SM<float>::st(buf + off, __uint_as_float(y[2 * gidx]), __uint_as_float(y[2 * gidx + 1]));
         }

@@ -129,9 +129,9 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
                 // earlier sections of this state must be complete
                 const int st = s_bop[p].state, need = s_bop[p].op;
                 if (ld_acquire(&ops_done[st]) < need) {
-                    const uint64_t t0 = ptx::globaltimer();
+                    const int64_t t0 = clock64(), lim = ptx::wait_cycles(kWaitLimitNs);
                     while (ld_acquire(&ops_done[st]) < need) {
-                        if (ptx::globaltimer() - t0 > kWaitLimitNs || *(volatile int *)err) {
+                        if (clock64() - t0 > lim || *(volatile int *)err) {
                             atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
                             s_abort[p] = 1;
                             break;

@@ -28,7 +28,7 @@
 // the host picks which chunk bits the lanes of a half-warp (quarter-warp for complex128)
 // enumerate so that their slots fall in distinct banks.
 //
-// Every wait is bounded (globaltimer); on expiry the kernel records DEV_ERR_TIMEOUT in the
+// Every wait is bounded (SM clock cycles); on expiry the kernel records DEV_ERR_TIMEOUT in the
 // error word and stops.
 #include <cuda.h>
 

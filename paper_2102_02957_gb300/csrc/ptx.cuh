@@ -27,31 +27,35 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// A thread whose phase is not complete yet is suspended until it completes, for at most
+// kSuspendNs (the hint), instead of returning at once: a waiting warp does not take issue slots
+// from the warps that work.
+constexpr uint32_t kSuspendNs = 1000000;  // 1 ms
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
 
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+// Bounded waits count SM clock cycles (a local counter, read in a few cycles).  A limit in
+// nanoseconds becomes 2 cycles per ns: about the limit at the 2.07 GHz maximum clock, longer at
+// lower clocks.
+__device__ __forceinline__ int64_t wait_cycles(uint64_t limit_ns) { return (int64_t)limit_ns * 2; }
 
-// Wait for the phase with the given parity to complete; give up after `limit_ns`.
+// Wait for the phase with the given parity to complete; give up after about `limit_ns`.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
+    const int64_t t0 = clock64(), lim = wait_cycles(limit_ns);
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > limit_ns) return false;
+        if (clock64() - t0 > lim) return false;
     }
 }
 
