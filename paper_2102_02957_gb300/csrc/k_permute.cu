@@ -21,6 +21,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnitsPerCta = 1024;  // 16-byte units per side staged in shared memory
 constexpr int kMaxItems = 128;      // outer items per batch (tiles are at least 8 units)
+constexpr int kLoadsPerThread = kUnitsPerCta / kThreads;
 
 struct PermArgs {
     int vbits;        // |V|
@@ -41,7 +42,7 @@ __device__ __forceinline__ int64_t insert0(int64_t x, int p) {
 }
 
 template <typename T2>
-__global__ void __launch_bounds__(kThreads) k_permute(T2 *a, PermArgs P) {
+__global__ void __launch_bounds__(kThreads, 4) k_permute(T2 *a, PermArgs P) {
     constexpr int apu = 16 / sizeof(T2);  // amplitudes per 16-byte unit
     __shared__ __align__(16) T2 sA[kUnitsPerCta * apu];
     __shared__ __align__(16) T2 sB[kUnitsPerCta * apu];
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_permute(T2 *a, PermArgs P) {
     __shared__ int s_mode[kMaxItems];  // 0 skip, 1 self, 2 exchange
 
     const int T = 1 << P.vbits;
-    const int upt = T / apu;  // units per tile
+    const int lg_upt = P.vbits - (apu == 2 ? 1 : 0);
+    const int upt = 1 << lg_upt;  // units per tile (T / apu)
     const int64_t nbatch = (P.nitems + P.ib - 1) / P.ib;
 
     for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
@@ -75,25 +77,38 @@ __global__ void __launch_bounds__(kThreads) k_permute(T2 *a, PermArgs P) {
         }
         __syncthreads();
 
+        // every unit of this thread is loaded into registers before any is staged, so that all of
+        // its loads are in flight at once (a batch has at most kUnitsPerCta = kLoadsPerThread *
+        // kThreads units per side)
         const int units = P.ib * upt;
-        for (int u = threadIdx.x; u < units; u += kThreads) {
-            const int it = u / upt, ut = u - it * upt;
+        uint4 xs[kLoadsPerThread], ys[kLoadsPerThread];
+#pragma unroll
+        for (int k = 0; k < kLoadsPerThread; ++k) {
+            const int u = threadIdx.x + k * kThreads;
+            if (u >= units) continue;
+            const int it = u >> lg_upt, ut = u & (upt - 1);
             const int mode = s_mode[it];
             if (!mode) continue;
             const int v0 = ut * apu;
             int64_t off = v0 & ((1 << P.L0) - 1);
             for (int j = 0; j < P.nextra; ++j) off |= int64_t((v0 >> (P.L0 + j)) & 1) << P.vpos[P.L0 + j];
-            const uint4 x = *reinterpret_cast<const uint4 *>(a + s_base[it] + off);
-            *reinterpret_cast<uint4 *>(sA + (size_t)it * T + v0) = x;
-            if (mode == 2) {
-                const uint4 y = *reinterpret_cast<const uint4 *>(a + s_base2[it] + off);
-                *reinterpret_cast<uint4 *>(sB + (size_t)it * T + v0) = y;
-            }
+            xs[k] = *reinterpret_cast<const uint4 *>(a + s_base[it] + off);
+            if (mode == 2) ys[k] = *reinterpret_cast<const uint4 *>(a + s_base2[it] + off);
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadsPerThread; ++k) {
+            const int u = threadIdx.x + k * kThreads;
+            if (u >= units) continue;
+            const int it = u >> lg_upt;
+            const int mode = s_mode[it];
+            if (!mode) continue;
+            *reinterpret_cast<uint4 *>(sA + (size_t)u * apu) = xs[k];
+            if (mode == 2) *reinterpret_cast<uint4 *>(sB + (size_t)u * apu) = ys[k];
         }
         __syncthreads();
 
         for (int u = threadIdx.x; u < units; u += kThreads) {
-            const int it = u / upt, ut = u - it * upt;
+            const int it = u >> lg_upt, ut = u & (upt - 1);
             const int mode = s_mode[it];
             if (!mode) continue;
             const int v0 = ut * apu;
