@@ -130,6 +130,11 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         return outside == 0 ? (g.vmask & blocked) == 0
                             : g.diag && (g.vmask & chosen & blocked) == 0 && (outside & out_blocked) == 0;
     };
+    // Once every chunk qubit is blocked no later gate is taken (each touches a chunk qubit, unless
+    // it is a diagonal gate wholly outside the chunk, possible with diag_outside only), so the scan
+    // stops there with the same count.
+    bool any_diag = false;
+    for (const PG &g : remaining) any_diag = any_diag || g.diag;
     auto absorbed = [&](uint64_t chosen, size_t limit) {
         uint64_t blocked = 0, out_blocked = 0;
         int k = 0;
@@ -140,6 +145,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             } else {
                 if (g.vmask & chosen) blocked |= g.vmask;
                 out_blocked |= g.vmask & ~chosen;
+                if (!any_diag && (blocked & chosen) == chosen) break;
             }
         }
         return k;
@@ -348,14 +354,22 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
         return mk;
     };
     const int rr = std::min(r, width);
+    // a gate with no chunk bit (a diagonal wholly outside the chunk) fits every group
+    bool any_outside = false;
+    for (const BlockGate &g : gates) any_outside = any_outside || mask_of(g) == 0;
     // gates a group on `bits` takes: in order, those inside `bits` and not behind a deferred gate
+    // (once all of `bits` are blocked no later gate fits, unless it has no chunk bit)
     auto takes = [&](uint64_t bits) {
         uint64_t blocked = 0;
         int k = 0;
         for (int32_t idx : pending) {
             const uint64_t mk = mask_of(gates[idx]);
-            if ((mk & ~bits) == 0 && (mk & blocked) == 0) ++k;
-            else blocked |= mk;
+            if ((mk & ~bits) == 0 && (mk & blocked) == 0) {
+                ++k;
+            } else {
+                blocked |= mk;
+                if (!any_outside && (blocked & bits) == bits) break;
+            }
         }
         return k;
     };
