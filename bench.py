@@ -2,7 +2,7 @@
 """Benchmark of the cache-blocked state-vector simulator on GB300.
 
 Workload (default): quantum-volume circuit, n = 30 qubits, depth 30 (450 Haar SU(4) gates),
-complex64 state (8 GiB), chunk c = 13 gathered with 4 pinned bits, tensor-core register groups,
+complex64 state (8 GiB), chunk c = 12 gathered with 5 pinned bits, tensor-core register groups,
 look-ahead chunk choice (the paper's rule is timed alongside).  One step = build the gate
 records, plan the cache blocking (host), reset the state to |0..0>, apply the circuit on the
 cache-blocked path, and read the norm back.  Metric: gates per second (higher is better), plus effective HBM bandwidth

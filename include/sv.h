@@ -92,7 +92,14 @@ typedef struct sv_options {
                                from the pinned bits and the first gate by the pending gate whose qubits
                                let the section take the most gates -- instead of the paper's priority
                                rule.  A heuristic of this library, not the paper's.  default 0 */
-    int32_t reserved[6];
+    int32_t tc_no_renorm;   /* 1: leave out the norm restoration of tensor-core circuits (the state is
+                               rescaled to its input norm after the last section when every fused
+                               group is unitary), so the result shows the raw 3xTF32 error.  default 0 */
+    int32_t wait_limit_ms;  /* bound of every device-side wait of the blocking kernels in milliseconds;
+                               on expiry the kernel stops and the next synchronising call returns
+                               SV_ERR_TIMEOUT.  0: the default (4000 ms).  Taken by sv_apply_circuit
+                               from the plan's options. */
+    int32_t reserved[4];
 } sv_options;
 
 void sv_options_default(sv_options *opts);

@@ -255,7 +255,7 @@ class Batch:
 
 
 _OPT_KEYS = ("chunk_bits", "reserve", "restore_layout", "seg_bits", "use_tc", "use_model", "threads", "gather_pinned",
-             "diag_outside", "lookahead")
+             "diag_outside", "lookahead", "tc_no_renorm", "wait_limit_ms")
 
 
 def batch_tune(states, gate_lists, **base):

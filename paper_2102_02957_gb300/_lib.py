@@ -28,7 +28,8 @@ class sv_options(ctypes.Structure):
     _fields_ = [("chunk_bits", ctypes.c_int32), ("reserve", ctypes.c_int32), ("restore_layout", ctypes.c_int32),
                 ("seg_bits", ctypes.c_int32), ("use_tc", ctypes.c_int32), ("use_model", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("gather_pinned", ctypes.c_int32), ("diag_outside", ctypes.c_int32),
-                ("lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("lookahead", ctypes.c_int32), ("tc_no_renorm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class sv_plan_info(ctypes.Structure):

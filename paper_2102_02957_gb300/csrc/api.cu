@@ -83,15 +83,18 @@ struct BlockProg {
     bool gathered = false;
 };
 
-// Tensor-core programs: every register group of a section becomes one fused unitary.  A
-// section whose B operands (8 KiB per group) would not fit next to the chunk ring in shared
-// memory is split into consecutive sweeps of at most kMaxTcSegs groups.  Appended after the
-// section programs: the composer's work list and the FP64 gate records it reads.
-constexpr int kMaxTcSegs = 11;
+// Tensor-core programs: every register group (r bits) of a section becomes one fused unitary.  A
+// section whose B operands (tc_b_bytes(r) per group: 2, 8 or 32 KiB) would not fit next to the
+// chunk ring in shared memory is split into consecutive sweeps of at most max_tc_segs(r) groups.
+// Appended after the section programs: the composer's work list and the FP64 gate records it
+// reads.
+static int max_tc_segs(int r) { return r == 3 ? 24 : r == 4 ? 11 : 3; }
 
-static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::vector<unsigned char> &host,
+static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r, std::vector<unsigned char> &host,
                               std::vector<BlockProg> &progs, size_t &cs_off, int &ncs, size_t &g_off,
                               size_t &flag_off) {
+    const int kMaxTcSegs = max_tc_segs(r);
+    const int b_bytes = tc_b_bytes(r);
     host.clear();
     progs.clear();
     auto align = [&](size_t a) {
@@ -114,7 +117,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::ve
         }
         for (const BlockGate &g : local.gates)
             if (g.ext[0] >= 0 || g.ext[1] >= 0) fail(SV_ERR_PLAN, "tensor-core sections take no gates outside the chunk");
-        const std::vector<HostSeg> segs = segment_block(local.gates, width, 4, 8);
+        const std::vector<HostSeg> segs = segment_block(local.gates, width, r, 8);
         for (size_t p0 = 0; p0 < segs.size(); p0 += kMaxTcSegs) {
             const size_t p1 = std::min(segs.size(), p0 + (size_t)kMaxTcSegs);
             BlockProg bp{};
@@ -140,7 +143,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::ve
             }
             align(16);
             const size_t b_base = host.size();
-            host.resize(host.size() + (size_t)bp.nseg * TC_B_BYTES, 0);
+            host.resize(host.size() + (size_t)bp.nseg * b_bytes, 0);
             for (size_t k = p0; k < p1; ++k) {
                 ComposeSeg c{};
                 c.flag_off = kNoFlag;
@@ -152,7 +155,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, std::ve
                     dg.push_back(g);
                 }
                 c.g1 = (int32_t)dg.size();
-                c.b_off = (uint32_t)(b_base + (k - p0) * TC_B_BYTES);
+                c.b_off = (uint32_t)(b_base + (k - p0) * b_bytes);
                 cs.push_back(c);
             }
             progs.push_back(bp);
@@ -507,12 +510,14 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         }
         std::vector<unsigned char> host;
         std::vector<BlockProg> progs;
-        const int seg_bits = h->dtype == SV_C64 ? plan->seg_bits : 4;
-        // tensor cores: complex64 with chunks of at least 11 bits (128-row tiles of 4-bit groups)
-        const bool tc = plan->use_tc && h->dtype == SV_C64 && std::min(plan->c, plan->n) - plan->reserve >= 11;
+        // SIMT register groups: 4 bits, or 5 for complex64
+        const int seg_bits = (h->dtype == SV_C64 && plan->seg_bits == 5) ? 5 : 4;
+        // tensor cores: complex64 with chunks of at least 128 rows of the plan's r-bit groups
+        const int tc_bits = plan->seg_bits;
+        const bool tc = plan->use_tc && h->dtype == SV_C64 && std::min(plan->c, plan->n) - plan->reserve >= tc_bits + 7;
         size_t cs_off = 0, g_off = 0, flag_off = 0;
         int ncs = 0;
-        if (tc) build_programs_tc(plan, gates, host, progs, cs_off, ncs, g_off, flag_off);
+        if (tc) build_programs_tc(plan, gates, tc_bits, host, progs, cs_off, ncs, g_off, flag_off);
         else if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
         else build_programs<double>(plan, gates, seg_bits, host, progs);
         upload_program(h, host);
@@ -524,12 +529,17 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         // input norm at the end: the radial error is removed, the unbiased rest stays.
         const int nb_norm = reduce_blocks(h->n);
         int *unitary_flag = tc ? reinterpret_cast<int *>(static_cast<unsigned char *>(h->prog) + flag_off) : nullptr;
+        const bool renorm = tc && !plan->tc_no_renorm;
         if (tc) {  // fuse every register group into its B operand, in FP64 on the GPU
             ensure_scratch(h, (size_t)(2 * nb_norm + 2) * sizeof(double));
-            launch_compose(base + cs_off, ncs, base + g_off, h->prog, unitary_flag, h->stream);
-            launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb_norm, h->stream);
-            st.kernel_launches += 2;
+            launch_compose(base + cs_off, ncs, base + g_off, h->prog, unitary_flag, tc_bits, h->stream);
+            ++st.kernel_launches;
         }
+        if (renorm) {
+            launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb_norm, h->stream);
+            ++st.kernel_launches;
+        }
+        const uint64_t wait_ns = plan->wait_limit_ms > 0 ? (uint64_t)plan->wait_limit_ms * 1000000ull : kDefaultWaitNs;
         size_t bi = 0;
         for (size_t oi = 0; oi < plan->ops.size(); ++oi) {
             const PlanOp &op = plan->ops[oi];
@@ -539,13 +549,13 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
                     mark_begin(h, 1, (int)oi);
                     if (tc)
                         launch_block_tc(h->amp, h->n, plan->c, bp.gathered ? &bp.lay : nullptr, base + bp.off, bp.nseg,
-                                        h->dev_err, h->stream);
+                                        h->dev_err, tc_bits, h->stream, wait_ns);
                     else if (!bp.gathered)
                         launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
-                                     seg_bits, h->stream);
+                                     seg_bits, h->stream, wait_ns);
                     else
                         launch_block_gather(h->dtype, h->amp, h->n, bp.lay, base + bp.off, bp.nseg, bp.ngate,
-                                            h->dev_err, seg_bits, h->stream);
+                                            h->dev_err, seg_bits, h->stream, wait_ns);
                     mark_end(h);
                     ++st.sweeps_block;
                     ++st.kernel_launches;
@@ -559,7 +569,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
             }
             ++st.kernel_launches;
         }
-        if (tc) {
+        if (renorm) {
             launch_partial_norm(h->dtype, h->amp, h->n, h->scratch + nb_norm, nb_norm, h->stream);
             launch_renorm(h->dtype, h->amp, h->n, h->scratch, nb_norm, unitary_flag,
                           reinterpret_cast<float *>(h->scratch + 2 * nb_norm), h->stream);

@@ -368,7 +368,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
         unsigned char *gdev = tmp + ((cs_bytes + 255) & ~size_t(255));
         if (g_bytes) check_cuda(cudaMemcpy(gdev, compose_gates.data(), g_bytes, cudaMemcpyHostToDevice), "H2D");
         try {
-            launch_compose(tmp, (int)compose.size(), gdev, b->dev + b->off_progs, nullptr, b->work);
+            launch_compose(tmp, (int)compose.size(), gdev, b->dev + b->off_progs, nullptr, 4, b->work);
             check_cuda(cudaStreamSynchronize(b->work), "cudaStreamSynchronize");
         } catch (...) {
             cudaFree(tmp);

@@ -375,32 +375,68 @@ __device__ __forceinline__ void run_segment(uint32_t buf, uint32_t seg, uint32_t
     }
 }
 
-constexpr uint64_t kTcWaitLimitNs = 4000000000ull;  // bounded waits of the tensor-core groups (4 s)
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+// x rounded to the nearest TF32 value (ties away from zero), as a bit pattern: adding half a TF32
+// unit in the last place to the magnitude bits and clearing the 13 dropped bits (a carry into the
+// exponent is the correct result).  Two integer operations instead of a conversion instruction.
+__device__ __forceinline__ uint32_t tf32_round(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
+// Shapes of a tensor-core register group of R bits (complex64): a row is the group's 2^R
+// amplitudes as K = 2^(R+1) reals; a tile is 128 rows.  TMEM columns of one tile buffer:
+// A_hi [0, K), A_lo [K, 2K), D [2K, 4K).  The B operand (TcGeom::B_BYTES, see TC_B_BYTES) is
+// B_hi then B_lo, K-major without swizzle, SBO bytes between 8-column groups, so the two stack
+// along N: one descriptor reads [B_hi | B_lo] as a K x 2K matrix.
+template <int R>
+struct TcGeom {
+    static constexpr int NA = 1 << R;
+    static constexpr int K = 2 * NA;
+    static constexpr int COLS = 4 * K;
+    static constexpr int KSTEPS = K / 8;
+    static constexpr int SBO = 32 * K;
+    static constexpr int B_BYTES = 8 * K * K;
+};
+
+template <int NR>
+__device__ __forceinline__ void tmem_st_n(uint32_t taddr, const uint32_t *r) {
+    if constexpr (NR == 16) {
+        ptx::tmem_st16(taddr, r);
+    } else {
+        ptx::tmem_st16(taddr, r);
+        ptx::tmem_st16(taddr + 16, r + 16);
+    }
+}
+template <int NR>
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t *o) {
+    if constexpr (NR == 16) {
+        ptx::tmem_ld16(taddr, o);
+    } else {
+        ptx::tmem_ld16(taddr, o);
+        ptx::tmem_ld16(taddr + 16, o + 16);
+    }
 }
 
-// Tensor-core register group (complex64, 4 bits): the group's fused unitary, stored as the
-// real-embedded B operand (B_hi at `bhi`, B_lo at bhi + 4096), is applied on tiles of 128
-// register groups: every thread writes its group's 32 reals split into TF32 high and low parts
-// to its TMEM lane (A_hi, A_lo), one thread issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo
-// (3 x 4 MMAs, M = 128, N = K = 32, FP32 accumulation), and every thread reads its row of D back.
-// NB (1 or 2) tiles are in flight per group; TMEM columns of tile buffer k: A_hi [tcol + 96k, +32),
-// A_lo [+32, +64), D [+64, +96); `mbar[k]` signals its MMAs' completion.
+// Tensor-core register group (complex64, R bits): the group's fused unitary, stored as the
+// real-embedded B operand at `bhi` (B_hi, then B_lo), is applied on tiles of 128 rows.  Every
+// thread splits its row x into A_hi = x rounded to nearest TF32 and A_lo = x - A_hi (exact in
+// FP32; the tensor cores read it truncated to TF32, an error of either sign since A_lo has
+// either sign), writes both to its TMEM lane, and one thread issues
+//     D[:, 0:2K]  = A_hi [B_hi | B_lo]      (K/8 MMAs, N = 2K)
+//     D[:, 0:K]  += A_lo B_hi               (K/8 MMAs, N = K)
+// with FP32 accumulation; the row's result is D[:, 0:K] + D[:, K:2K] = A_hi B_hi + A_lo B_hi +
+// A_hi B_lo (3xTF32).  Stacking B_hi and B_lo along N makes 2K/8 MMAs per tile instead of 3K/8:
+// an MMA of N <= 128 costs its issuing thread about the same time whatever N is.
+// NB (1 or 2) tiles are in flight per group; `mbar[k]` signals buffer k's MMAs' completion.
 //
-// RENORM: the tensor cores' FP32 accumulation truncates, shrinking each result by a few units
-// in the last place the same way every time.  Callers that cannot restore the state's norm once
-// per circuit set RENORM: for a group whose fused matrix is unitary (the int after B_lo is
-// nonzero) each output row is rescaled to its input row's norm, as y <- y (1 + d) with
-// d = (|x|^2 - |y|^2) / (2 |y|^2) (a scale factor rounded next to 1 would itself be biased).
-template <int NC, bool RENORM = false, int NB = 2>
+// RENORM: callers that cannot restore the state's norm once per circuit set RENORM: for a group
+// whose fused matrix is unitary (the int after the B operand is nonzero) each output row is
+// rescaled to its input row's norm, as y <- y (1 + d) with d = (|x|^2 - |y|^2) / (2 |y|^2).
+template <int R, int NC, bool RENORM = false, int NB = 2>
 __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint32_t bhi, int ctid, const int *swz,
                                                int c, uint32_t tcol, int bar_id, uint64_t *mbar, uint32_t (&phase)[2],
-                                               volatile int *abort_flag) {
-    constexpr int R = 4, NA = 16;
+                                               volatile int *abort_flag, const uint64_t *wait_ns) {
+    using G = TcGeom<R>;
+    constexpr int NA = G::NA, K = G::K;
+    constexpr int CH = 8;  // amplitudes per TMEM access batch (16 columns): fewer live registers
     int po[R], pf[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -408,32 +444,36 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         po[j] = 1 << p;
         pf[j] = po[j] ^ swz[p];
     }
-    const int lane = ctid & 31;
-    int lbase = 0, lfb = 0;
+    // A thread's row in tile t is row t * NC + ctid: its low 5 bits (the lane) pick lane bits, the
+    // next two (the warp in the group, NC = 128) the first two rest bits, and the bits above (t)
+    // rest bits 2, 3, ...; the warp's part is folded in here, the tile's read per tile.
+    static_assert(NC == 128, "a tile is 128 rows: 4 warps of 32");
+    const int lane = ctid & 31, wg = ctid >> 5;
+    int wbase = 0, wfb = 0;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         const int p = lds_s8(seg + 8 + j);
-        if ((lane >> j) & 1) { lbase |= 1 << p; lfb ^= swz[p]; }
+        if ((lane >> j) & 1) { wbase |= 1 << p; wfb ^= swz[p]; }
     }
-    const int nrest = lds_s8(seg + 13), flags = lds_s8(seg + 14);
-    int rpo[kMaxRest], rpf[kMaxRest];
 #pragma unroll
-    for (int j = 0; j < kMaxRest; ++j) {
-        const int p = j < nrest ? lds_s8(seg + 16 + j) : 0;
-        rpo[j] = j < nrest ? 1 << p : 0;
-        rpf[j] = j < nrest ? swz[p] : 0;
+    for (int j = 0; j < 2; ++j) {
+        const int p = lds_s8(seg + 16 + j);
+        if ((wg >> j) & 1) { wbase |= 1 << p; wfb ^= swz[p]; }
     }
+    const int flags = lds_s8(seg + 14);
     const int T = (1 << (c - R)) / NC;  // 128-row tiles per chunk
     const uint32_t lane_off = (uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16;  // this thread's TMEM lane
-    constexpr uint32_t idesc = ptx::idesc_tf32(128, 32);
+    constexpr uint32_t idesc_wide = ptx::idesc_tf32(128, 2 * K), idesc_narrow = ptx::idesc_tf32(128, K);
 
     // group base (natural and swizzled) of this thread's row in tile t
     auto row_base = [&](int t, int &base, int &sbase) {
-        const int hi = (t * NC + ctid) >> 5;
-        int bs = lbase, fb = lfb;
-#pragma unroll
-        for (int j = 0; j < kMaxRest; ++j)
-            if ((hi >> j) & 1) { bs |= rpo[j]; fb ^= rpf[j]; }
+        int bs = wbase, fb = wfb;
+        for (int j = 0; (t >> j) != 0; ++j)
+            if ((t >> j) & 1) {
+                const int p = lds_s8(seg + 18 + j);
+                bs |= 1 << p;
+                fb ^= swz[p];
+            }
         base = bs;
         sbase = bs ^ fb;
     };
@@ -445,32 +485,38 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         ld_step[j] = (uint32_t)((flags & 1) ? po[j] : pf[j]) << 3;
         st_step[j] = (uint32_t)((flags & 2) ? po[j] : pf[j]) << 3;
     }
-    // tile t -> TMEM buffer k.  A_hi is the amplitude itself (the tensor cores read it as the
-    // truncated TF32 value), A_lo the exact remainder x - trunc_tf32(x).  Returns the row base.
     bool failed = false;
-    const bool renorm = RENORM && lds_s32(bhi + 8192) != 0;
+    const bool renorm = RENORM && lds_s32(bhi + G::B_BYTES) != 0;
+    // tile t -> TMEM buffer k; returns the row base
     auto stage = [&](int t, int k, int &base, int &sbase, float &nrm) -> bool {
         row_base(t, base, sbase);
-        uint32_t ahi[32], alo[32];
         nrm = 0.f;
+        const uint32_t col = tcol + (uint32_t)k * G::COLS + lane_off;
         // byte offset inside the chunk (< chunk bytes: every step flips bits below 2^c * 8); the
         // buffer base is only 1 KiB aligned, so it is added after the XOR walk, never XORed
         uint32_t off = (uint32_t)((flags & 1) ? base : sbase) << 3;
 #pragma unroll
-        for (int b = 0; b < NA; ++b) {
-            if (b) off ^= ld_step[low_bit(b)];
-            const int gidx = b ^ (b >> 1);  // Gray code: this amplitude's local index
-            float xr, xi;
-            SM<float>::ld(buf + off, xr, xi);
-            ahi[2 * gidx] = __float_as_uint(xr);
-            ahi[2 * gidx + 1] = __float_as_uint(xi);
-            alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(__float_as_uint(xr) & 0xFFFFE000u));
-            alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(__float_as_uint(xi) & 0xFFFFE000u));
-            if (RENORM) nrm = fmaf(xr, xr, fmaf(xi, xi, nrm));
+        for (int h = 0; h < NA / CH; ++h) {
+            // Gray steps [h CH, h CH + CH) visit the amplitudes [g CH, g CH + CH), g = gray(h)
+            const int g = h ^ (h >> 1);
+            uint32_t ahi[2 * CH], alo[2 * CH];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int b = h * CH + q;
+                if (b) off ^= ld_step[low_bit(b)];
+                const int gidx = (b ^ (b >> 1)) - g * CH;  // Gray code: this amplitude's index in the batch
+                float xr, xi;
+                SM<float>::ld(buf + off, xr, xi);
+                const uint32_t hr = tf32_round(xr), hi_ = tf32_round(xi);
+                ahi[2 * gidx] = hr;
+                ahi[2 * gidx + 1] = hi_;
+                alo[2 * gidx] = __float_as_uint(xr - __uint_as_float(hr));
+                alo[2 * gidx + 1] = __float_as_uint(xi - __uint_as_float(hi_));
+                if (RENORM) nrm = fmaf(xr, xr, fmaf(xi, xi, nrm));
+            }
+            tmem_st_n<2 * CH>(col + (uint32_t)(2 * CH * g), ahi);
+            tmem_st_n<2 * CH>(col + (uint32_t)(K + 2 * CH * g), alo);
         }
-        const uint32_t col = tcol + (uint32_t)k * 96;
-        ptx::tmem_st32(col + lane_off, ahi);
-        ptx::tmem_st32(col + 32 + lane_off, alo);
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
         // every row of the tile is in TMEM; the barrier also tells the group whether any
@@ -478,16 +524,14 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
         if (ptx::named_bar_or(bar_id, NC, failed)) return false;
         if (ctid == 0) {
             ptx::tc_fence_after();
+            const uint32_t a = tcol + (uint32_t)k * G::COLS, d = a + 2 * K;
+            // step s reads B rows [8s, 8s + 8): 256 bytes on, i.e. 16 in the descriptor's address
+            // field (shared addresses stay below 2^18, so the field never carries over)
+            const uint64_t bd = ptx::smem_desc_kmajor(bhi, 128, G::SBO);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, s > 0);
+            for (int s = 0; s < G::KSTEPS; ++s) ptx::mma_tf32_ts(d, a + 8 * s, bd + 16 * s, idesc_wide, s > 0);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                ptx::mma_tf32_ts(col + 64, col + 32 + 8 * s, ptx::smem_desc_kmajor(bhi + 256 * s, 128, 1024), idesc, 1);
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-                ptx::mma_tf32_ts(col + 64, col + 8 * s, ptx::smem_desc_kmajor(bhi + 4096 + 256 * s, 128, 1024), idesc,
-                                 1);
+            for (int s = 0; s < G::KSTEPS; ++s) ptx::mma_tf32_ts(d, a + K + 8 * s, bd + 16 * s, idesc_narrow, 1);
             ptx::mma_commit(&mbar[k]);
         }
         return true;
@@ -495,35 +539,56 @@ __device__ __forceinline__ bool run_segment_tc(uint32_t buf, uint32_t seg, uint3
     // wait for buffer k's product and write the tile (row base `base`/`sbase`) back to the chunk
     // (after an expired wait the tile is garbage; the group stops at its next barrier)
     auto finish = [&](int k, int base, int sbase, float nrm) {
-        if (!ptx::mbar_wait(&mbar[k], phase[k], kTcWaitLimitNs)) {
+        if (!ptx::mbar_wait(&mbar[k], phase[k], *(volatile const uint64_t *)wait_ns)) {
             failed = true;
             *abort_flag = 1;
         }
         phase[k] ^= 1;
         ptx::tc_fence_after();
-        uint32_t y[32];
-        ptx::tmem_ld32(tcol + (uint32_t)k * 96 + 64 + lane_off, y);
-        ptx::tmem_wait_ld();
+        const uint32_t dcol = tcol + (uint32_t)k * G::COLS + 2 * K + lane_off;
+        float ny = 0.f, dsc = 0.f;
         if (RENORM && renorm) {
-            float ny = 0.f;
+            // the row's output norm first (a second pass over TMEM), then the scale
 #pragma unroll
-            for (int q = 0; q < 32; ++q) ny = fmaf(__uint_as_float(y[q]), __uint_as_float(y[q]), ny);
-            const float d = ny > 0.f ? 0.5f * (nrm - ny) / ny : 0.f;
+            for (int h = 0; h < NA / CH; ++h) {
+                uint32_t y0[2 * CH], y1[2 * CH];
+                tmem_ld_n<2 * CH>(dcol + (uint32_t)(2 * CH * h), y0);
+                tmem_ld_n<2 * CH>(dcol + (uint32_t)(K + 2 * CH * h), y1);
+                ptx::tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; ++q) y[q] = __float_as_uint(fmaf(__uint_as_float(y[q]), d, __uint_as_float(y[q])));
+                for (int q = 0; q < 2 * CH; ++q) {
+                    const float v = __uint_as_float(y0[q]) + __uint_as_float(y1[q]);
+                    ny = fmaf(v, v, ny);
+                }
+            }
+            dsc = ny > 0.f ? 0.5f * (nrm - ny) / ny : 0.f;
         }
         uint32_t off = (uint32_t)((flags & 2) ? base : sbase) << 3;
 #pragma unroll
-        for (int b = 0; b < NA; ++b) {
-            if (b) off ^= st_step[low_bit(b)];
-            const int gidx = b ^ (b >> 1);
-            SM<float>::st(buf + off, __uint_as_float(y[2 * gidx]), __uint_as_float(y[2 * gidx + 1]));
+        for (int h = 0; h < NA / CH; ++h) {
+            const int g = h ^ (h >> 1);
+            uint32_t y0[2 * CH], y1[2 * CH];
+            tmem_ld_n<2 * CH>(dcol + (uint32_t)(2 * CH * g), y0);
+            tmem_ld_n<2 * CH>(dcol + (uint32_t)(K + 2 * CH * g), y1);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int b = h * CH + q;
+                if (b) off ^= st_step[low_bit(b)];
+                const int gidx = (b ^ (b >> 1)) - g * CH;
+                float yr = __uint_as_float(y0[2 * gidx]) + __uint_as_float(y1[2 * gidx]);
+                float yi = __uint_as_float(y0[2 * gidx + 1]) + __uint_as_float(y1[2 * gidx + 1]);
+                if (RENORM && renorm) {
+                    yr = fmaf(yr, dsc, yr);
+                    yi = fmaf(yi, dsc, yi);
+                }
+                SM<float>::st(buf + off, yr, yi);
+            }
         }
     };
-    // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
     int pb, ps;
     float pn;
-    if constexpr (NB == 2) {
+    if constexpr (NB == 2) {  // two tiles in flight: tile t is staged (and its MMAs issued) while tile t-1's run
         if (!stage(0, 0, pb, ps, pn)) return false;
         for (int t = 1; t < T; ++t) {
             int nb, ns;

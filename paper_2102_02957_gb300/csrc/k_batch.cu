@@ -19,6 +19,7 @@ namespace sv {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
+__device__ const uint64_t kBatchWaitNs = kWaitLimitNs;  // bound of the tensor-core groups' waits
 // Threads per CTA: 256 for SIMT-only batches, 128 (one 128-row tensor-core tile) when sections
 // run on the tensor cores.
 constexpr int RB = 4;     // register-group width
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
     }
     __syncthreads();
     if constexpr (TC) ptx::tc_fence_after();
-    const uint32_t tmem_pool = TC ? s_tmem + (uint32_t)(p * 192) : 0u;
+    const uint32_t tmem_pool = TC ? s_tmem + (uint32_t)(p * 2 * TcGeom<4>::COLS) : 0u;
     uint32_t mma_phase[2] = {0, 0};
     BatchOp &op = s_bop[p];
     while (true) {
@@ -189,9 +190,10 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
                     // fused group on the tensor cores, unbiased per row (the batch has no
                     // per-circuit norm restoration); the return value is uniform over the pool
                     if constexpr (TC) {
-                        if (!run_segment_tc<NT, true>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)),
+                        if (!run_segment_tc<4, NT, true>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)),
                                                       body_s + (uint32_t)(si * kBatchTcGroupBytes), ctid, c_swz64, ce,
-                                                      tmem_pool, 1 + p, s_mma[p], mma_phase, &s_tc_abort[p])) {
+                                                      tmem_pool, 1 + p, s_mma[p], mma_phase, &s_tc_abort[p],
+                                                      &kBatchWaitNs)) {
                             tc_failed = true;
                             break;
                         }

@@ -53,9 +53,13 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     plan->c = c;
     plan->reserve = o.reserve;
     plan->restore = o.restore_layout ? 1 : 0;
-    plan->seg_bits = (o.seg_bits == 4 || o.seg_bits == 5) ? o.seg_bits : 4;
+    // register-group width: 4 or 5 bits (3 too for tensor-core groups)
+    plan->seg_bits = (o.seg_bits == 4 || o.seg_bits == 5 || (o.seg_bits == 3 && o.use_tc)) ? o.seg_bits : 4;
     plan->use_tc = o.use_tc;
     plan->pinned = pinned;
+    plan->tc_no_renorm = o.tc_no_renorm ? 1 : 0;
+    if (o.wait_limit_ms < 0) { delete plan; fail(SV_ERR_ARG, "wait_limit_ms must be >= 0"); }
+    plan->wait_limit_ms = o.wait_limit_ms;
     plan->keys.reserve((size_t)n_gates);
 
     std::vector<int32_t> lab(n);
@@ -217,7 +221,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             };
             add_candidate(chosen);
             // smaller chunks (still room for a 2-qubit gate; >= 11 bits for the tensor-core path)
-            const int min_t = std::max(pinned + 2, (o.use_tc && dtype == SV_C64) ? 11 : 1);
+            const int min_t = std::max(pinned + 2, (o.use_tc && dtype == SV_C64) ? plan->seg_bits + 7 : 1);
             for (int d = 1; d <= 2; ++d)
                 if (target - d >= min_t && target - d >= remaining.front().nq + pinned) add_candidate(rule_select(target - d));
             add_candidate(greedy_select(target));
@@ -679,8 +683,8 @@ void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gate
     } else {
         loc = localize_gates(op, n, plan.c, nullptr);
     }
-    const bool tc = plan.use_tc && dtype == SV_C64 && ce >= 11;
-    const int r = tc ? 4 : (dtype == SV_C64 ? plan.seg_bits : 4);
+    const bool tc = plan.use_tc && dtype == SV_C64 && ce >= plan.seg_bits + 7;
+    const int r = tc ? plan.seg_bits : (dtype == SV_C64 && plan.seg_bits == 5 ? 5 : 4);
     const int nseg = loc.empty() ? 0 : (int)segment_block(loc, ce, r, 8).size();
     int q_total = 0, two = 0, cheap = 0;
     float hist[6] = {0, 0, 0, 0, 0, 0};

@@ -53,6 +53,7 @@ struct GateKey {
 
 struct sv_plan {
     int32_t n = 0, c = 0, reserve = 0, restore = 1, seg_bits = 4, use_tc = 0, pinned = 0;
+    int32_t tc_no_renorm = 0, wait_limit_ms = 0;  // executor options carried by the plan
     std::vector<sv::PlanOp> ops;
     std::vector<int32_t> final_map;
     std::vector<sv::GateKey> keys;  // structure of the gate list it was made from
@@ -177,11 +178,14 @@ std::vector<BlockGate> localize_gates(const PlanOp &op, int n, int c, const Gath
 // Tensor-core path: per register group, the gates to fuse and where its B operand goes.
 struct ComposeSeg {
     int32_t g0, g1;     // gate range in the FP64 gate array
-    uint32_t b_off;     // byte offset of the group's B_hi (B_lo follows at +4096) in the program
+    uint32_t b_off;     // byte offset of the group's B_hi (B_lo follows at + tc_b_bytes(r) / 2) in the program
     uint32_t flag_off;  // where to write an int: 1 if the fused matrix is unitary (kNoFlag: none)
 };
 constexpr uint32_t kNoFlag = 0xFFFFFFFFu;
-constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one register group (2 x 32 x 32 TF32)
+constexpr int TC_B_BYTES = 8192;  // B_hi + B_lo of one 4-bit register group (2 x 32 x 32 TF32)
+// B_hi + B_lo of an r-bit group: two K x K TF32 matrices, K = 2^(r+1) reals per row.
+constexpr int tc_b_bytes(int r) { return 8 << (2 * (r + 1)); }
+static_assert(tc_b_bytes(4) == TC_B_BYTES, "B operand size");
 
 // Batched execution: one blocking section of one state.  Chunk-local bit k is state bit k for
 // k < low (the contiguous low run of the chunk) and high[k - low] above it; the chunk index
@@ -203,9 +207,9 @@ constexpr int kBatchTcGroupBytes = TC_B_BYTES + 16;  // B operand + unitarity fl
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
                   int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int use_tc,
                   int *dev_err, cudaStream_t st);
-// Fuse the register groups in FP64; *all_unitary (1 on entry; may be null) is cleared when a
-// fused matrix is not unitary to 1e-10 (max |U^H U - I|).
-void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary,
+// Fuse register groups of r bits in FP64; *all_unitary (1 on entry; may be null) is cleared when
+// a fused matrix is not unitary to 1e-10 (max |U^H U - I|).
+void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary, int r,
                     cudaStream_t st);
 
 // cost-model network kernels (k_mlp.cu)
@@ -230,16 +234,18 @@ struct PermPlan;  // defined in k_permute.cu
 void launch_permute(int dtype, void *state, int n, const std::vector<std::pair<int32_t, int32_t>> &pairs,
                     cudaStream_t st);
 
+// Bounded device waits: wait_ns (kDefaultWaitNs unless the plan sets wait_limit_ms).
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;
 void launch_block(int dtype, void *state, int n, int c, const void *dev_prog, int nseg, int ngates, int *dev_err,
-                  int seg_bits, cudaStream_t st);
+                  int seg_bits, cudaStream_t st, uint64_t wait_ns = kDefaultWaitNs);
 // Blocking section over a gathered chunk (bits in `mask`), fetched and written back with
 // tensor copies.
 void launch_block_gather(int dtype, void *state, int n, const GatherLayout &lay, const void *dev_prog, int nseg,
-                         int ngates, int *dev_err, int seg_bits, cudaStream_t st);
-// Tensor-core blocking section (complex64, 4-bit register groups, B operands in the program);
-// `lay` null for a contiguous chunk of c bits.
+                         int ngates, int *dev_err, int seg_bits, cudaStream_t st, uint64_t wait_ns = kDefaultWaitNs);
+// Tensor-core blocking section (complex64, register groups of seg_bits = 3, 4 or 5 bits, B
+// operands in the program, tc_b_bytes(seg_bits) each); `lay` null for a contiguous chunk of c bits.
 void launch_block_tc(void *state, int n, int c, const GatherLayout *lay, const void *dev_prog, int nseg, int *dev_err,
-                     cudaStream_t st);
+                     int seg_bits, cudaStream_t st, uint64_t wait_ns = kDefaultWaitNs);
 size_t devgate_bytes(int dtype);
 
 // readouts

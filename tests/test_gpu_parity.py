@@ -306,6 +306,34 @@ def test_tensor_core_quantum_volume_24(sv, c):
     assert_close(got, ref, "c64")
 
 
+@pytest.mark.parametrize("r", [3, 4, 5])
+@pytest.mark.parametrize("n,c,pinned", [(12, 12, 0), (14, 12, 0), (20, 12, 4), (24, 12, 5), (17, 13, 0), (21, 13, 4)])
+def test_tensor_core_group_widths(sv, r, n, c, pinned):
+    """Fused groups of r = 3, 4 and 5 bits (8x8, 16x16 and 32x32 unitaries; real embeddings of
+    K = 16, 32, 64) applied as 3xTF32 MMAs, with and without the per-circuit norm restoration,
+    against the oracle: single-chunk, contiguous (chunk_swap) and gathered layouts."""
+    desc = _mixed(n, 120, 700 + n + c + r) + cg.quantum_volume(n, 6, n + r)
+    ref = sim.simulate(n, desc, 5)
+    for raw in (0, 1):
+        got = _run(sv, n, desc, "c64", basis=5,
+                   plan_opts=dict(chunk_bits=c, gather_pinned=pinned, use_tc=1, seg_bits=r, tc_no_renorm=raw))
+        assert_close(got, ref, "c64")
+
+
+def test_tensor_core_width_needs_room(sv):
+    """A 5-bit tensor-core group needs 128 rows of 32 amplitudes: with 11-bit chunks the plan runs on
+    SIMT register groups of 5 bits instead, still on the GPU and still exact to the tolerance."""
+    n = 14
+    desc = cg.quantum_volume(n, 2, 1)
+    gates = sv.make_gates(desc)
+    with sv.StateVector(n, "c64") as st:
+        st.init_basis(0)
+        plan = sv.Plan(n, gates, chunk_bits=11, use_tc=1, seg_bits=5)
+        st.apply(gates, plan)
+        st.synchronize()
+        assert_close(st.get_state(), sim.simulate(n, desc), "c64")
+
+
 def _diag_rich(n, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
