@@ -37,6 +37,13 @@ section while some of its qubits are outside the chunk, because those qubits are
 chunk -- the gate acts there as a diagonal on its chunk qubits, or as a phase.  It is taken when
 its chunk qubits are not in QB_BLOCKED and no earlier deferred gate touches its outside qubits.
 
+Look-ahead chunk choice (``lookahead``, gathered chunks only; not in the paper, which notes that
+better schedules exist): QB_CHUNK starts as the first remaining gate's qubits and the pinned
+qubits, then grows one pending gate at a time: among the first 512 remaining gates, the first 64
+distinct sets of qubits that a gate would add (and that still fit) are tried, and the set with
+which a QB_BLOCKED scan of those 512 gates takes the most gates is added (the first such set on a
+tie); when nothing fits, the remaining places are filled with qubits by ascending physical bit.
+
 Gathered chunks (``pinned > 0``): the same loop without data movement.  A chunk is any set of c
 bits that contains the low ``pinned`` bits; the section gathers it from HBM instead of having
 chunk_swap rounds make it contiguous.  QB_CHUNK starts as the pinned qubits and is filled by the
@@ -111,8 +118,99 @@ def _canonical_qubits(kind, qubits):
 DIAGONAL_KINDS = ("z", "rz", "cp", "cz")
 
 
+LOOKAHEAD_WINDOW = 512   # remaining gates a look-ahead scan inspects
+LOOKAHEAD_CHOICES = 64   # distinct candidate qubit sets tried per growth step
+
+
+def _scan_takes(remaining, chosen_set, diag, limit):
+    """Number of gates a QB_BLOCKED scan of the first `limit` remaining gates would put in a
+    section whose chunk holds `chosen_set` (the scan of the planner loop below, counting only)."""
+    blocked, out_blocked, taken = set(), set(), 0
+    for gi, qs in remaining[:limit]:
+        outside = [q for q in qs if q not in chosen_set]
+        if not outside:
+            take = not any(q in blocked for q in qs)
+        else:
+            take = (gi in diag and not any(q in blocked for q in qs if q in chosen_set)
+                    and not any(q in out_blocked for q in outside))
+        if take:
+            taken += 1
+        else:
+            if any(q in chosen_set for q in qs):
+                blocked.update(qs)
+            out_blocked.update(outside)
+    return taken
+
+
+def _lookahead_chunk(remaining, target, pinned_qubits, diag, fill_order):
+    """QB_CHUNK by look-ahead: the first remaining gate's qubits and the pinned ones, then, step by
+    step, the candidate qubit set (new qubits of one of the first LOOKAHEAD_WINDOW remaining
+    gates; the first LOOKAHEAD_CHOICES distinct sets that fit) whose scan takes the most gates;
+    finally filled in `fill_order`."""
+    chosen = set(remaining[0][1]) | set(pinned_qubits)
+    while len(chosen) < target:
+        best, best_score, tried = None, -1, []
+        for _gi, qs in remaining[:LOOKAHEAD_WINDOW]:
+            if len(tried) >= LOOKAHEAD_CHOICES:
+                break
+            fresh = frozenset(qs) - chosen
+            if not fresh or len(chosen) + len(fresh) > target or fresh in tried:
+                continue
+            tried.append(fresh)
+            score = _scan_takes(remaining, chosen | fresh, diag, LOOKAHEAD_WINDOW)
+            if score > best_score:
+                best, best_score = fresh, score
+        if best is None:
+            break
+        chosen |= best
+    for q in fill_order:
+        if len(chosen) >= target:
+            break
+        chosen.add(q)
+    return chosen
+
+
+def _rule_chunk(remaining, target, pinned, pinv, n, width):
+    """QB_CHUNK by the priority rule (Sec. IV.A with the readings in the module docstring)."""
+    chosen, chosen_set = [], set()
+
+    def try_add(qs):
+        new = []
+        for q in qs:
+            if q not in chosen_set and q not in new:
+                new.append(q)
+        if len(chosen) + len(new) <= target:
+            chosen.extend(new)
+            chosen_set.update(new)
+
+    for p in range(pinned):  # gathered chunks always hold the low `pinned` bits
+        try_add((pinv[p],))
+    try_add(remaining[0][1])
+    for _gi, qs in remaining:
+        if len(chosen) >= target:
+            break
+        if len(qs) > 1:
+            try_add(qs)
+    for _gi, qs in remaining:
+        if len(chosen) >= target:
+            break
+        if len(qs) == 1:
+            try_add(qs)
+    for p in range(n if pinned else width):
+        if len(chosen) >= target:
+            break
+        try_add((pinv[p],))
+    return chosen, chosen_set
+
+
 def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool = True, pinned: int = 0,
-                  diag_outside: bool = False) -> Plan:
+                  diag_outside: bool = False, lookahead: bool = False, steer=None, steer_min_chunk: int = 0) -> Plan:
+    """`steer` (gathered chunks only): a function that receives, for every section, the candidate
+    chunk qubit sets -- the priority rule's chunk, the rule's chunk one and two qubits smaller
+    (when at least `steer_min_chunk` (default pinned + 2) and still room for the first remaining
+    gate beside the pinned qubits), and the look-ahead chunk, duplicates dropped in that order --
+    and returns the index of the one to use.  This is the candidate set a cost model chooses
+    from; the choice itself is the caller's."""
     if not (1 <= n <= 62):
         raise ValueError("n out of range")
     if c < 1:
@@ -153,35 +251,28 @@ def plan_blocking(n: int, gates, c: int, reserve: int = 0, restore_layout: bool 
 
     while remaining:
         # -- choose QB_CHUNK
-        chosen = []
-        chosen_set = set()
+        if pinned and steer is not None:
+            cands = []
 
-        def try_add(qs):
-            new = []
-            for q in qs:
-                if q not in chosen_set and q not in new:
-                    new.append(q)
-            if len(chosen) + len(new) <= target:
-                chosen.extend(new)
-                chosen_set.update(new)
+            def add(cs):
+                if cs not in cands:
+                    cands.append(cs)
 
-        for p in range(pinned):  # gathered chunks always hold the low `pinned` bits
-            try_add((pinv[p],))
-        try_add(remaining[0][1])
-        for _gi, qs in remaining:
-            if len(chosen) >= target:
-                break
-            if len(qs) > 1:
-                try_add(qs)
-        for _gi, qs in remaining:
-            if len(chosen) >= target:
-                break
-            if len(qs) == 1:
-                try_add(qs)
-        for p in range(n if pinned else width):
-            if len(chosen) >= target:
-                break
-            try_add((pinv[p],))
+            add(frozenset(_rule_chunk(remaining, target, pinned, pinv, n, width)[1]))
+            min_chunk = steer_min_chunk or pinned + 2
+            for d in (1, 2):
+                if target - d >= min_chunk and target - d >= len(remaining[0][1]) + pinned:
+                    add(frozenset(_rule_chunk(remaining, target - d, pinned, pinv, n, width)[1]))
+            add(frozenset(_lookahead_chunk(remaining, target, [pinv[p] for p in range(pinned)], diag,
+                                           [pinv[p] for p in range(n)])))
+            chosen_set = set(cands[steer(cands)])
+            chosen = sorted(chosen_set)
+        elif pinned and lookahead:
+            chosen_set = _lookahead_chunk(remaining, target, [pinv[p] for p in range(pinned)], diag,
+                                          [pinv[p] for p in range(n)])
+            chosen = sorted(chosen_set)
+        else:
+            chosen, chosen_set = _rule_chunk(remaining, target, pinned, pinv, n, width)
 
         # -- chunk_swap round (none for gathered chunks: the section gathers its bits)
         incoming = [] if pinned else sorted(q for q in chosen if m[q] >= width)

@@ -130,6 +130,56 @@ def test_steered_plan_gives_oracle_state(sv, trained, use_tc):
             assert_close(st.get_state(), sim.simulate(n, desc), "c64")
 
 
+def _sections(stream):
+    """(chunk mask, gate indices) of every gathered section in a serialised library plan."""
+    it = iter(stream)
+    _n, _c, _reserve, _restore, nops = (next(it) for _ in range(5))
+    out = []
+    for _ in range(nops):
+        kind = next(it)
+        if kind in (1, 3):
+            cnt = next(it)
+            for _ in range(2 * cnt):
+                next(it)
+        else:
+            mask = next(it) if kind == 4 else None
+            cnt = next(it)
+            gis = []
+            for _ in range(cnt):
+                gi, _nq, _p0, _p1 = next(it), next(it), next(it), next(it)
+                gis.append(gi)
+            out.append((mask, gis))
+    return out
+
+
+@pytest.mark.parametrize("use_tc", [0, 1])
+def test_steered_schedule_is_one_of_the_oracle_candidates(sv, trained, use_tc):
+    """Each section of a steered plan is one of the candidate chunks the oracle restates (the
+    rule at the full chunk and one and two qubits smaller, and the look-ahead chunk), and given
+    those choices the whole schedule equals the oracle's bit for bit.  The choice among the
+    candidates is the network's and is not restated."""
+    from oracle import planner
+    n, c, pinned = 20, 13, 4
+    for desc in (cg.random_layers(n, 10, 77), cg.quantum_volume(n, 6, 78), cg.quantum_volume(n, 10, 79)):
+        g = sv.make_gates(desc)
+        plan = sv.Plan(n, g, model=trained, chunk_bits=c, gather_pinned=pinned, use_tc=use_tc)
+        stream = plan.serialize()
+        want = [mask for mask, _ in _sections(stream)]
+        picks = []
+
+        def steer(cands):
+            k = len(picks)
+            masks = [sum(1 << q for q in cs) for cs in cands]
+            assert k < len(want) and want[k] in masks, (k, want[k:k + 1], masks)
+            picks.append(masks.index(want[k]))
+            return picks[-1]
+
+        q = planner.plan_blocking(n, desc, c, pinned=pinned, steer=steer,
+                                  steer_min_chunk=max(pinned + 2, 4 + 7 if use_tc else 1))
+        assert q.serialize() == stream
+        print(f"use_tc={use_tc}: {len(picks)} sections, candidate picked per section {picks}")
+
+
 def _time_ms(sv, st, g, plan, reps=5):
     import torch
     ts = []
@@ -147,8 +197,9 @@ def _time_ms(sv, st, g, plan, reps=5):
 
 
 def test_steered_planner_gain_on_held_out_circuits(sv, trained):
-    """Held-out circuits at n = 26: the steered plan's measured time against the paper's rule
-    (same options).  The steered planner must not lose beyond timing noise; the gain is printed."""
+    """Held-out circuits at n = 26: the steered plan's measured time (median of 5 runs) against the
+    paper's rule and against the look-ahead chunk choice, same options.  The steered planner must
+    beat the rule by more than timing noise (2 %); its standing against look-ahead is printed."""
     n = 26
     rows = []
     with sv.StateVector(n, "c64") as st:
@@ -157,13 +208,18 @@ def test_steered_planner_gain_on_held_out_circuits(sv, trained):
             for tc in (0, 1):
                 o = dict(chunk_bits=13, gather_pinned=4, use_tc=tc)
                 rule = sv.Plan(n, g, **o)
+                look = sv.Plan(n, g, lookahead=1, **o)
                 steer = sv.Plan(n, g, model=trained, **o)
                 t_rule = _time_ms(sv, st, g, rule)
+                t_look = _time_ms(sv, st, g, look)
                 t_steer = _time_ms(sv, st, g, steer)
-                rows.append((tc, rule.info().n_blocks, steer.info().n_blocks, t_rule, t_steer))
-    for tc, nb_r, nb_s, tr, ts in rows:
-        print(f"tc={tc} sections rule={nb_r} steered={nb_s}  ms rule={tr:.3f} steered={ts:.3f}  gain={tr / ts:.3f}x")
-    total_rule = sum(r[3] for r in rows)
-    total_steer = sum(r[4] for r in rows)
-    print(f"total gain {total_rule / total_steer:.3f}x")
-    assert total_steer <= 1.03 * total_rule
+                rows.append((tc, rule.info().n_blocks, look.info().n_blocks, steer.info().n_blocks, t_rule, t_look,
+                             t_steer))
+    for tc, nb_r, nb_l, nb_s, tr, tl, ts in rows:
+        print(f"tc={tc} sections rule={nb_r} look-ahead={nb_l} steered={nb_s}  ms rule={tr:.3f} "
+              f"look-ahead={tl:.3f} steered={ts:.3f}  gain vs rule {tr / ts:.3f}x, vs look-ahead {tl / ts:.3f}x")
+    total_rule = sum(r[4] for r in rows)
+    total_look = sum(r[5] for r in rows)
+    total_steer = sum(r[6] for r in rows)
+    print(f"total gain vs rule {total_rule / total_steer:.3f}x, vs look-ahead {total_look / total_steer:.3f}x")
+    assert total_steer <= 0.98 * total_rule

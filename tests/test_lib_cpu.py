@@ -197,11 +197,38 @@ def _plan_from_stream(stream, pinned):
     return plan
 
 
+@pytest.mark.parametrize("n,c,pinned", [(6, 4, 1), (8, 5, 1), (10, 6, 2), (12, 8, 4), (14, 9, 3), (16, 10, 4),
+                                        (30, 12, 5), (30, 13, 4)])
+def test_planner_schedule_parity_lookahead(sv, n, c, pinned):
+    """The look-ahead chunk choice: the library's schedules equal the oracle's restatement bit for
+    bit, with and without diagonal gates outside the chunk."""
+    for desc in _circuits(n, 11 * n + c):
+        gates = sv.make_gates(desc)
+        for diag in (0, 1):
+            p = sv.Plan(n, gates, chunk_bits=c, gather_pinned=pinned, lookahead=1, diag_outside=diag)
+            q = planner.plan_blocking(n, desc, c, pinned=pinned, lookahead=True, diag_outside=bool(diag))
+            assert p.serialize() == q.serialize(), (n, c, pinned, diag)
+
+
+@pytest.mark.parametrize("name,c,pinned", [("qv30", 12, 5), ("qv32", 13, 4), ("rl28", 12, 5), ("qft28", 12, 4),
+                                           ("rl32", 13, 4)])
+def test_planner_schedule_parity_lookahead_full_size(sv, name, c, pinned):
+    """The schedules behind the benchmark (quantum volume n = 30, chunk 12 with 5 pinned bits) and
+    the other full-size workloads, look-ahead chunk choice, against the oracle bit for bit."""
+    w = cg.WORKLOADS[name]
+    desc = cg.build(name)
+    gates = sv.make_gates(desc)
+    for diag in (0, 1):
+        p = sv.Plan(w["n"], gates, chunk_bits=c, gather_pinned=pinned, lookahead=1, diag_outside=diag)
+        q = planner.plan_blocking(w["n"], desc, c, pinned=pinned, lookahead=True, diag_outside=bool(diag))
+        assert p.serialize() == q.serialize(), (name, diag)
+
+
 @pytest.mark.parametrize("n,c,pinned", [(10, 6, 2), (12, 8, 4), (14, 9, 3)])
 def test_lookahead_plans_valid_and_equivalent(sv, n, c, pinned):
     """The look-ahead chunk choice (a heuristic of this library, not the paper's rule) yields valid
     schedules that simulate to the original circuit, with no more sections than the rule on
-    these circuits; checked on the oracle side (no GPU)."""
+    these circuits (no GPU)."""
     for desc in _circuits(n, 5 * n + c):
         gates = sv.make_gates(desc)
         for diag in (0, 1):

@@ -82,3 +82,44 @@ def test_dead_unit_has_zero_gradient():
     g = mlp.unpack(mlp.gradient(th, X, T)[0])
     assert np.all(g["W1"][5] == 0.0) and g["b1"][5] == 0.0
     assert np.all(g["W2"][:, 5] == 0.0)
+
+
+def test_adam_constant_gradient_every_step():
+    """Adam with the same gradient g at every step: m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2
+    (geometric sums from zero moments), so the bias-corrected mhat = g and vhat = g^2 at every t,
+    and each step moves theta by -lr * g / (|g| + eps).  A wrong exponent in a bias correction, or
+    a step count starting at 0, breaks this from t = 2 on."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    theta0 = rng.normal(size=mlp.N_PARAMS)
+    g = rng.normal(size=mlp.N_PARAMS)
+    lr = 3e-3
+    theta, m, v = theta0.copy(), np.zeros_like(g), np.zeros_like(g)
+    for t in range(1, 6):
+        theta, m, v = mlp.adam_step(theta, m, v, g, t, lr)
+        np.testing.assert_allclose(theta, theta0 - t * lr * g / (np.abs(g) + mlp.EPS), rtol=1e-11, atol=1e-14)
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+
+
+def test_adam_three_steps_hand_computed():
+    """One parameter, gradients 1, -2, 1/2, lr = 0.1, from theta = 0 and zero moments, worked out
+    in exact fractions (b1 = 9/10, b2 = 999/1000):
+      t = 1: m = 1/10, v = 1/1000; mhat = m / (1 - b1) = 1, vhat = v / (1 - b2) = 1;
+             theta = -0.1 * 1 / (1 + 1e-8)
+      t = 2: m = 9/10 * 1/10 - 2/10 = -11/100, v = 999/1000 * 1/1000 + 4/1000 = 4999/10^6;
+             mhat = m / (1 - 81/100) = -11/19, vhat = v / (1 - 998001/10^6) = 4999/1999
+      t = 3: m = 9/10 * (-11/100) + 1/20 = -49/1000, v = 999/1000 * 4999/10^6 + 1/4000
+             = 5244001/10^9; mhat = m / (1 - 729/1000) = -49/271,
+             vhat = v / (1 - 997002999/10^9) = 749143/428143
+    theta_t = theta_{t-1} - 0.1 * mhat / (sqrt(vhat) + 1e-8)."""
+    want_theta = [-0.09999999900000000999999990000000099999999,
+                  -0.06338964652792491179449285107285070167998,
+                  -0.04972058032617827440666908045065548322021]
+    want_m = [1 / 10, -11 / 100, -49 / 1000]
+    want_v = [1 / 1000, 4999 / 1e6, 5244001 / 1e9]
+    theta, m, v = np.zeros(1), np.zeros(1), np.zeros(1)
+    for t, gt in enumerate((1.0, -2.0, 0.5), 1):
+        theta, m, v = mlp.adam_step(theta, m, v, np.array([gt]), t, 0.1)
+        assert m[0] == pytest.approx(want_m[t - 1], rel=1e-14)
+        assert v[0] == pytest.approx(want_v[t - 1], rel=1e-13)
+        assert theta[0] == pytest.approx(want_theta[t - 1], rel=1e-13, abs=1e-16)

@@ -190,3 +190,39 @@ def test_diag_outside_qft_needs_one_section_per_chunk_of_hadamards():
         base = planner.plan_blocking(n, gates, c, pinned=pinned)
         assert p.n_blocks == math.ceil((n - pinned) / (c - pinned)), (c, pinned, p.n_blocks)
         assert p.n_blocks < base.n_blocks
+
+
+def test_lookahead_hand_worked_example():
+    """Look-ahead chunk choice on a case worked out by hand (n = 8, chunk of 5 qubits, qubit 0
+    pinned).  Gates: g0 = CX(1,2), g1 = CX(3,4), g2..g5 = CX(5,6).
+    Rule (Sec. IV.A priority): {0} + g0's {1,2} + the next multi-qubit gate that fits, g1's {3,4}
+    -> section 1 takes g0, g1; section 2 starts {0} + {5,6} and fills by ascending bit 1, 2.
+    Look-ahead: start {0,1,2}; candidate {3,4} lets a QB_BLOCKED scan take g0, g1 (2 gates),
+    candidate {5,6} takes g0, g2, g3, g4, g5 (5 gates; g1 is deferred without blocking anything)
+    -> section 1 = {0,1,2,5,6} with g0, g2..g5; section 2 = {0,3,4} filled with 1, 2."""
+    desc = [("cx", (1, 2), ()), ("cx", (3, 4), ())] + [("cx", (5, 6), ())] * 4
+    la = planner.plan_blocking(8, desc, 5, pinned=1, lookahead=True)
+    assert la.ops == [
+        ("gblock", (0b1100111, [(0, (1, 2)), (2, (5, 6)), (3, (5, 6)), (4, (5, 6)), (5, (5, 6))])),
+        ("gblock", (0b0011111, [(1, (3, 4))])),
+    ]
+    rule = planner.plan_blocking(8, desc, 5, pinned=1)
+    assert rule.ops == [
+        ("gblock", (0b0011111, [(0, (1, 2)), (1, (3, 4))])),
+        ("gblock", (0b1100111, [(2, (5, 6)), (3, (5, 6)), (4, (5, 6)), (5, (5, 6))])),
+    ]
+
+
+@pytest.mark.parametrize("n,c,pinned", [(8, 5, 1), (10, 6, 2), (12, 8, 4), (14, 9, 3)])
+def test_lookahead_plans_valid_and_equivalent_oracle(n, c, pinned):
+    """The oracle's own look-ahead schedules: valid, and simulating them (sections on their
+    chunk bits, then the reordering) gives the original circuit's state."""
+    rng_seed = 31 * n + c
+    circuits = [cg.random_layers(n, 4, rng_seed), cg.quantum_volume(n, 5, rng_seed), cg.qft(n),
+                cg.hea(n, 2, rng_seed, 1), cg.noisy_trajectory(n, 3, 0.3, rng_seed, 2)]
+    for desc in circuits:
+        for diag in (False, True):
+            plan = planner.plan_blocking(n, desc, c, pinned=pinned, lookahead=True, diag_outside=diag)
+            planner.validate(plan, desc, diag_outside=diag)
+            ref = sim.simulate(n, desc, 3)
+            assert np.abs(sim.execute_plan(n, desc, plan, 3) - ref).max() < 1e-12
