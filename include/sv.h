@@ -204,8 +204,11 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
  * kernel) is captured once into a CUDA graph and replayed on later runs with the same flags;
  * SV_BATCH_FROM_ZERO -- every state starts from |0..0> (Sec. IV.C initial state): the first
  * section writes its chunks from the basis state instead of reading them, so the amplitudes
- * need no prior sv_init_basis. */
-enum { SV_BATCH_GRAPH = 1, SV_BATCH_FROM_ZERO = 2 };
+ * need no prior sv_init_basis.  SV_BATCH_TEST_STALL -- a test of the failure path: the first
+ * section of the batch's first state never releases that state's later sections, so their
+ * bounded waits (opts->wait_limit_ms of sv_batch_create, default 4000 ms) expire; the launch ends
+ * and sv_batch_sync returns SV_ERR_TIMEOUT.  Not combinable with SV_BATCH_GRAPH. */
+enum { SV_BATCH_GRAPH = 1, SV_BATCH_FROM_ZERO = 2, SV_BATCH_TEST_STALL = 4 };
 sv_status sv_batch_run(sv_batch_h batch, int32_t flags);
 /* Wait for the last run; SV_ERR_TIMEOUT if a bounded wait in the launch expired. */
 sv_status sv_batch_sync(sv_batch_h batch);

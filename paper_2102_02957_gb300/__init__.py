@@ -228,9 +228,11 @@ class Batch:
         o = options(**opts)
         check(lib().sv_batch_create(cnt, hs, gp, ng, ctypes.byref(o), ctypes.byref(self._h)))
 
-    def run(self, use_graph: bool = False, from_zero: bool = False):
-        """One launch; from_zero: every state starts from |0..0> (no sv_init_basis needed)."""
-        flags = (_lib.SV_BATCH_GRAPH if use_graph else 0) | (_lib.SV_BATCH_FROM_ZERO if from_zero else 0)
+    def run(self, use_graph: bool = False, from_zero: bool = False, test_stall: bool = False):
+        """One launch; from_zero: every state starts from |0..0> (no sv_init_basis needed);
+        test_stall: SV_BATCH_TEST_STALL (a failure-path test: the launch times out)."""
+        flags = ((_lib.SV_BATCH_GRAPH if use_graph else 0) | (_lib.SV_BATCH_FROM_ZERO if from_zero else 0)
+                 | (_lib.SV_BATCH_TEST_STALL if test_stall else 0))
         check(lib().sv_batch_run(self._h, flags))
 
     def synchronize(self):

@@ -58,6 +58,7 @@ _lib = None
 # name -> (restype, argtypes)
 SV_BATCH_GRAPH = 1
 SV_BATCH_FROM_ZERO = 2
+SV_BATCH_TEST_STALL = 4
 SV_COSTMODEL_FEATURES = 16
 SV_COSTMODEL_PARAMS = 5313
 _VP = ctypes.c_void_p

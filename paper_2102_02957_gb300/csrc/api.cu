@@ -50,7 +50,7 @@ static void ensure_scratch(sv_state *h, size_t bytes) {
     h->scratch_bytes = bytes;
 }
 
-static void check_dev_error(sv_state *h) {
+void check_dev_error(sv_state *h) {
     int e = 0;
     check_cuda(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read error word");
     check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");

@@ -19,6 +19,7 @@ struct sv_batch {
     int64_t total = 0;
     double bytes = 0;
     int use_tc = 0;
+    uint64_t wait_ns = sv::kDefaultWaitNs;          // bound of the kernel's waits
     cudaGraph_t graph[2] = {nullptr, nullptr};     // per SV_BATCH_FROM_ZERO value
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<std::pair<void *, int>> idle;       // states without gates: (amplitudes, n)
@@ -38,7 +39,7 @@ struct sv_batch {
 namespace sv {
 namespace {
 
-void launch_once(sv_batch *b, int from_zero) {
+void launch_once(sv_batch *b, int from_zero, int stall = 0) {
     if (from_zero)
         for (const auto &z : b->idle) launch_init_basis(SV_C64, z.first, z.second, 0, b->work);
     unsigned char *c = b->dev + b->off_counters;
@@ -49,7 +50,7 @@ void launch_once(sv_batch *b, int from_zero) {
     int *err = reinterpret_cast<int *>(next + 1);
     launch_batch(b->dev + b->off_ops, b->nops, b->dev + b->off_progs,
                  reinterpret_cast<void *const *>(b->dev + b->off_amps), ops_done, chunks_done, next, b->total,
-                 from_zero, b->use_tc, err, b->work);
+                 from_zero, b->use_tc, err, b->work, b->wait_ns, stall ? 0 : -1);
 }
 
 int *batch_err(sv_batch *b) {
@@ -96,6 +97,8 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
 
     sv_options base;
     if (opts) base = *opts; else sv_options_default(&base);
+    if (base.wait_limit_ms < 0) fail(SV_ERR_ARG, "wait_limit_ms must be >= 0");
+    if (base.wait_limit_ms > 0) b->wait_ns = (uint64_t)base.wait_limit_ms * 1000000ull;
     std::vector<std::vector<BatchOp>> per_state((size_t)count);
     std::vector<unsigned char> progs;
     // tensor-core sections (complex64 chunks of >= 11 bits): groups fused in FP64 on the GPU
@@ -384,13 +387,16 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
 sv_status sv_batch_run(sv_batch_h b, int32_t flags) {
     SV_API_BEGIN
     if (!b) fail(SV_ERR_ARG, "null batch");
-    if (flags & ~(SV_BATCH_GRAPH | SV_BATCH_FROM_ZERO)) fail(SV_ERR_ARG, "sv_batch_run: unknown flag");
+    if (flags & ~(SV_BATCH_GRAPH | SV_BATCH_FROM_ZERO | SV_BATCH_TEST_STALL))
+        fail(SV_ERR_ARG, "sv_batch_run: unknown flag");
     const int use_graph = flags & SV_BATCH_GRAPH, fz = (flags & SV_BATCH_FROM_ZERO) ? 1 : 0;
+    const int stall = (flags & SV_BATCH_TEST_STALL) ? 1 : 0;
+    if (stall && use_graph) fail(SV_ERR_ARG, "sv_batch_run: SV_BATCH_TEST_STALL is not combinable with SV_BATCH_GRAPH");
     // the batch's stream follows the states' stream, and the states' stream follows the batch
     check_cuda(cudaEventRecord(b->ev_in, b->stream), "cudaEventRecord");
     check_cuda(cudaStreamWaitEvent(b->work, b->ev_in, 0), "cudaStreamWaitEvent");
     if (!use_graph) {
-        launch_once(b, fz);
+        launch_once(b, fz, stall);
     } else {
         if (!b->exec[fz]) {
             check_cuda(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");

@@ -18,8 +18,6 @@
 namespace sv {
 namespace {
 
-constexpr uint64_t kWaitLimitNs = 4000000000ull;
-__device__ const uint64_t kBatchWaitNs = kWaitLimitNs;  // bound of the tensor-core groups' waits
 // Threads per CTA: 256 for SIMT-only batches, 128 (one 128-row tensor-core tile) when sections
 // run on the tensor cores.
 constexpr int RB = 4;     // register-group width
@@ -80,7 +78,8 @@ template <int NT, int POOLS>
 __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const BatchOp *__restrict__ ops, int nops,
                                                       const unsigned char *__restrict__ progs, float2 *const *amps,
                                                       int *ops_done, int *chunks_done, unsigned long long *next,
-                                                      int64_t total, int from_zero, int prog_cap, int *err) {
+                                                      int64_t total, int from_zero, int prog_cap, int *err,
+                                                      uint64_t wait_ns, int stall_state) {
     constexpr bool TC = POOLS == 2;  // the tensor-core configuration
     extern __shared__ __align__(16) unsigned char smem[];
     const int p = threadIdx.x / NT, ctid = threadIdx.x % NT;
@@ -95,6 +94,8 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
     __shared__ uint64_t s_mma[POOLS][2];        // tensor-core tile buffers: MMAs complete
     __shared__ uint32_t s_tmem;
     __shared__ int s_tc_abort[POOLS];
+    __shared__ uint64_t s_wait_ns;  // the wait bound, read where a wait gives up
+    if (threadIdx.x == 0) s_wait_ns = wait_ns;
     if (ctid == 0) {
         s_cached[p] = -1;
         s_abort[p] = 0;
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
                 // earlier sections of this state must be complete
                 const int st = s_bop[p].state, need = s_bop[p].op;
                 if (ld_acquire(&ops_done[st]) < need) {
-                    const int64_t t0 = clock64(), lim = ptx::wait_cycles(kWaitLimitNs);
+                    const int64_t t0 = clock64(), lim = ptx::wait_cycles(wait_ns);
                     while (ld_acquire(&ops_done[st]) < need) {
                         if (clock64() - t0 > lim || *(volatile int *)err) {
                             atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
                         if (!run_segment_tc<4, NT, true>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)),
                                                       body_s + (uint32_t)(si * kBatchTcGroupBytes), ctid, c_swz64, ce,
                                                       tmem_pool, 1 + p, s_mma[p], mma_phase, &s_tc_abort[p],
-                                                      &kBatchWaitNs)) {
+                                                      &s_wait_ns)) {
                             tc_failed = true;
                             break;
                         }
@@ -221,7 +222,8 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
         if (ctid == 0) {
             if (atomicAdd(&chunks_done[s_op[p]], 1) == op.nchunks - 1) {
                 __threadfence();
-                atomicAdd(&ops_done[op.state], 1);  // section complete: release the state's next one
+                // section complete: release the state's next one (except the stall test's section)
+                if (!(op.state == stall_state && op.op == 0)) atomicAdd(&ops_done[op.state], 1);
             }
         }
     }
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
 
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
                   int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int use_tc,
-                  int *dev_err, cudaStream_t st) {
+                  int *dev_err, cudaStream_t st, uint64_t wait_ns, int stall_state) {
     const int prog_cap = use_tc ? kBatchMaxProgBytesTc : kBatchMaxProgBytes;
     const int pools = use_tc ? 2 : 1, nt = use_tc ? 128 : 256;
     const size_t smem = (size_t)pools * ((size_t(1) << kBatchMaxChunkBits) * sizeof(float2) + (size_t)prog_cap);
@@ -257,7 +259,7 @@ void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *co
     const int grid = num_sms() * per_sm;
     kern<<<grid, nt * pools, smem, st>>>((const BatchOp *)dev_ops, nops, (const unsigned char *)dev_progs,
                                          (float2 *const *)dev_amps, dev_ops_done, dev_chunks_done, dev_next, total,
-                                         from_zero, prog_cap, dev_err);
+                                         from_zero, prog_cap, dev_err, wait_ns, stall_state);
     check_cuda(cudaGetLastError(), "batch kernel launch");
 }
 

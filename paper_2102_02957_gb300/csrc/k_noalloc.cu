@@ -126,7 +126,8 @@ extern "C" sv_status sv_expval_pauli_noalloc(sv_handle h, uint64_t x, uint64_t z
         double res[2] = {0, 0};
         check_cuda(cudaMemcpyAsync(res, scratch + 2 * kMaxPartials, sizeof(res), cudaMemcpyDeviceToHost, h->stream),
                    "cudaMemcpyAsync(expval result)");
-        check_cuda(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        // synchronise and report a failure an earlier kernel on this handle left in its error word
+        check_dev_error(h);
         double sr = res[0], si = res[1];
         switch (__builtin_popcountll(x & z) & 3) {  // times i^{popc(x & z)}
             case 1: { const double t = sr; sr = -si; si = t; break; }

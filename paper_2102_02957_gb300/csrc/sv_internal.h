@@ -204,9 +204,11 @@ constexpr int kBatchMaxChunkBits = 13;
 constexpr int kBatchMaxProgBytes = 24 * 1024;    // program piece of a SIMT batch
 constexpr int kBatchMaxProgBytesTc = 32 * 1024;  // ... of a batch with tensor-core sections (per pool)
 constexpr int kBatchTcGroupBytes = TC_B_BYTES + 16;  // B operand + unitarity flag per group
+// wait_ns bounds every device wait; stall_state >= 0 (a failure-path test) keeps that state's first
+// section from releasing the later ones.
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
                   int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int use_tc,
-                  int *dev_err, cudaStream_t st);
+                  int *dev_err, cudaStream_t st, uint64_t wait_ns, int stall_state);
 // Fuse register groups of r bits in FP64; *all_unitary (1 on entry; may be null) is cleared when
 // a fused matrix is not unitary to 1e-10 (max |U^H U - I|).
 void launch_compose(const void *dev_segs, int nseg, const void *dev_gates, void *dev_prog, int *all_unitary, int r,
@@ -266,6 +268,12 @@ void launch_sample_within(int dtype, const void *state, int n, int sum_bits, con
 double splitmix_uniform(uint64_t seed, uint64_t s);
 
 int num_sms();
+
+}  // namespace sv
+struct sv_state;
+namespace sv {
+// Synchronise the handle's stream and turn its device error word into a status (clearing it).
+void check_dev_error(sv_state *h);
 
 }  // namespace sv
 

@@ -57,3 +57,32 @@ def test_noalloc_back_to_back_on_two_states(sv):
     finally:
         a.close()
         b.close()
+
+
+def test_noalloc_allocates_nothing(sv):
+    """The point of the entry point: after the first call on this device (which sets up the
+    library's fixed scratch), further calls on a fresh handle take no device memory -- neither the
+    handle's own scratch (which sv_expval_pauli would create) nor anything else: the device's
+    free bytes and torch's reserved bytes stay exactly the same."""
+    import torch
+    n = 16
+    g = sv.make_gates(cg.quantum_volume(n, 3, 6))
+    warm = sv.StateVector(10, "c64")
+    try:
+        warm.init_basis(1)
+        warm.expval_pauli_noalloc(0, 1)  # the first call on the device
+    finally:
+        warm.close()
+    with sv.StateVector(n, "c64") as st:
+        st.init_basis(0)
+        st.apply(g)
+        st.synchronize()
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        reserved0 = torch.cuda.memory_reserved()
+        vals = [st.expval_pauli_noalloc(x, z) for x, z in cg.random_pauli_strings(n, 6, 12)]
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
+        assert torch.cuda.memory_reserved() == reserved0
+        assert all(np.isfinite(v.real) and np.isfinite(v.imag) for v in vals)
