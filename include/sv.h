@@ -168,6 +168,47 @@ sv_status sv_plan_serialize(sv_plan_h plan, int64_t *buf, int64_t cap, int64_t *
  * have been made from the same n and gate list (SV_ERR_PLAN otherwise). */
 sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, sv_plan_h plan);
 
+/* ------------------------------------------------------------------ partitioned states */
+/* A state partitioned on its top qubits (Sec. II.B: the state vector is divided into pieces, one
+ * per process, on the highest qubits; Sec. IV.C: blocks run on each piece alone, and a
+ * chunk_swap of a chunk qubit with a partition qubit moves half of each piece to a partner,
+ * Fig. 10 case (a); the output reordering can also swap two partition qubits, Fig. 10 case (b)).
+ * One handle holds one piece: h->n = plan n - (partition qubits); its amplitude k is the state's
+ * amplitude (piece index << h->n) | k.
+ *
+ * Run plan ops [op_begin, op_end) of a plan made with gather_pinned = 0 (contiguous chunks) on
+ * the piece: blocking sections with SIMT register groups (the chunk must fit the piece: c <= h->n),
+ * and the chunk_swap / reordering pairs whose two bits are both below h->n.  Pairs with a bit at
+ * or above h->n are left to the caller, who exchanges data between pieces with sv_shard_pack /
+ * sv_shard_unpack.  With h->n == plan n this is a part of sv_apply_circuit (without its
+ * tensor-core sections).  Asynchronous on the handle's stream.  SV_ERR_PLAN for a plan of other
+ * gates or a chunk wider than the piece; SV_ERR_UNSUPPORTED for gathered-chunk plans. */
+sv_status sv_apply_plan_ops(sv_handle h, const sv_gate *gates, int64_t n_gates, sv_plan_h plan,
+                            int32_t op_begin, int32_t op_end);
+/* Copy the piece's amplitudes whose local bit `bit` equals `value` (0 or 1), in index order, to
+ * the DEVICE buffer dev_out (2^(h->n - 1) amplitudes), or back from dev_in into the same places.
+ * bit < 0 copies the whole piece (2^h->n amplitudes).  Asynchronous on the handle's stream; the
+ * buffers are the caller's. */
+sv_status sv_shard_pack(sv_handle h, int32_t bit, int32_t value, void *dev_out);
+sv_status sv_shard_unpack(sv_handle h, int32_t bit, int32_t value, const void *dev_in);
+
+/* ------------------------------------------------------------------ host-resident states */
+/* Apply a plan (made with gather_pinned = 0) to a state kept in HOST memory, with the GPU as a
+ * cache for its chunks (Sec. IV.C: chunks that do not fit in GPU memory stay in host memory and
+ * are staged through the GPU; Sec. V.B: 33 to 35 qubits that way).  host_amps: the caller's 2^n
+ * amplitudes (layout as sv_dtype; pinned memory lets the copies run at the link's rate).  The
+ * plan runs in passes, each streaming the state through the device work buffer once: consecutive
+ * sections and chunk_swap / reordering rounds share a pass when their sub-states fit half the
+ * buffer (two are in flight, so copies overlap kernels).  dev_work: a DEVICE buffer of work_bytes
+ * (the caller's), or NULL to let the library allocate work_bytes for the call; it must hold two
+ * sub-states of 2^(c+2) amplitudes unless it holds the whole state twice.  Sections run on SIMT
+ * register groups.  Synchronous: returns when the state in host memory is final.  passes (may be
+ * NULL): the number of passes over the state.  SV_ERR_PLAN / SV_ERR_UNSUPPORTED as for
+ * sv_apply_circuit and for gathered plans; SV_ERR_ARG for a work buffer that is too small. */
+sv_status sv_apply_circuit_host(int32_t n, int32_t dtype, void *host_amps, const sv_gate *gates,
+                                int64_t n_gates, sv_plan_h plan, void *dev_work, size_t work_bytes,
+                                void *cuda_stream, int32_t *passes);
+
 /* Statistics of the last sv_apply_circuit on this handle (host-side counts). */
 typedef struct sv_apply_stats {
     int64_t kernel_launches;

@@ -101,6 +101,20 @@ class Plan:
             pass
 
 
+def apply_host(n: int, host, gates: np.ndarray, plan: Plan, work_bytes: int, dtype="c64", dev_work=None,
+               stream=None) -> int:
+    """sv_apply_circuit_host: run `plan` on a state in host memory (`host`: a numpy array or a
+    pinned CPU torch tensor of 2^n amplitudes, updated in place) through a device work buffer of
+    work_bytes (dev_work: its address, or None to let the library allocate it).  Returns the
+    number of passes over the state."""
+    ptr = host.ctypes.data if isinstance(host, np.ndarray) else host.data_ptr()
+    s = getattr(stream, "cuda_stream", stream)
+    passes = ctypes.c_int32()
+    check(lib().sv_apply_circuit_host(n, DTYPES[dtype], ptr, gates.ctypes.data, len(gates), plan.handle, dev_work,
+                                      work_bytes, s, ctypes.byref(passes)))
+    return passes.value
+
+
 class StateVector:
     """n-qubit state on the GPU.  `buffer`: optional CUDA torch tensor that holds the amplitudes
     (caller-owned); `stream`: optional torch.cuda.Stream (or raw cudaStream_t int)."""
@@ -142,6 +156,18 @@ class StateVector:
     # -- execution
     def apply(self, gates: np.ndarray, plan: Plan | None = None):
         check(lib().sv_apply_circuit(self._h, gates.ctypes.data, len(gates), plan.handle if plan else None))
+
+    def apply_ops(self, gates: np.ndarray, plan: Plan, op_begin: int, op_end: int):
+        """sv_apply_plan_ops: plan ops [op_begin, op_end) on this state, which may be one piece of
+        a larger partitioned state (pairs that reach above this piece are skipped)."""
+        check(lib().sv_apply_plan_ops(self._h, gates.ctypes.data, len(gates), plan.handle, op_begin, op_end))
+
+    def pack(self, bit: int, value: int, dev_out: int) -> None:
+        """sv_shard_pack into the device buffer at dev_out (an integer address)."""
+        check(lib().sv_shard_pack(self._h, bit, value, dev_out))
+
+    def unpack(self, bit: int, value: int, dev_in: int) -> None:
+        check(lib().sv_shard_unpack(self._h, bit, value, dev_in))
 
     def set_profiling(self, on: bool = True):
         check(lib().sv_set_profiling(self._h, int(bool(on))))

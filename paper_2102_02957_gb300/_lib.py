@@ -77,6 +77,11 @@ _SIGS = {
     "sv_plan_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(sv_plan_info)]),
     "sv_plan_serialize": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sv_apply_circuit": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
+    "sv_apply_plan_ops": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "sv_shard_pack": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "sv_shard_unpack": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "sv_apply_circuit_host": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_int64, _VP, _VP,
+                                             ctypes.c_size_t, _VP, _VP]),
     "sv_get_apply_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sv_apply_stats)]),
     "sv_probabilities": (ctypes.c_int, [_VP, _VP, ctypes.c_int32]),
     "sv_norm2": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),

@@ -242,6 +242,15 @@ static void build_programs(const sv_plan *plan, const sv_gate *gates, int seg_bi
     align(256);
 }
 
+void build_simt_programs(const sv_plan *plan, const sv_gate *gates, int dtype, SimtPrograms &out) {
+    out.seg_bits = (dtype == SV_C64 && plan->seg_bits == 5) ? 5 : 4;
+    std::vector<BlockProg> progs;
+    if (dtype == SV_C64) build_programs<float>(plan, gates, out.seg_bits, out.host, progs);
+    else build_programs<double>(plan, gates, out.seg_bits, out.host, progs);
+    out.progs.clear();
+    for (const BlockProg &bp : progs) out.progs.push_back(SimtPrograms::Prog{bp.off, bp.nseg, bp.ngate, bp.op_index});
+}
+
 static void upload_program(sv_state *h, const std::vector<unsigned char> &host) {
     const size_t bytes = std::max<size_t>(host.size(), 256);
     if (h->prog_event) check_cuda(cudaEventSynchronize(h->prog_event), "cudaEventSynchronize");
@@ -578,6 +587,74 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
     }
     st.algorithmic_bytes = sweep * (double)(st.sweeps_block + st.sweeps_permute + st.sweeps_gate);
     h->stats = st;
+    SV_API_END
+}
+
+sv_status sv_apply_plan_ops(sv_handle h, const sv_gate *gates, int64_t n_gates, sv_plan_h plan, int32_t op_begin,
+                            int32_t op_end) {
+    SV_API_BEGIN
+    if (!h || !plan) fail(SV_ERR_ARG, "null argument");
+    if (plan->pinned) fail(SV_ERR_UNSUPPORTED, "sv_apply_plan_ops: plans with gathered chunks are not split into pieces");
+    if (plan->n < h->n) fail(SV_ERR_PLAN, "sv_apply_plan_ops: the plan has fewer qubits than the state");
+    if (std::min(plan->c, plan->n) > h->n) fail(SV_ERR_PLAN, "sv_apply_plan_ops: the chunk is wider than the state piece");
+    if (op_begin < 0 || op_end < op_begin || op_end > (int32_t)plan->ops.size()) fail(SV_ERR_ARG, "op range out of bounds");
+    validate_gates(plan->n, gates, n_gates);
+    if ((int64_t)plan->keys.size() != n_gates) fail(SV_ERR_PLAN, "plan was made for another gate list");
+    for (int64_t i = 0; i < n_gates; ++i) {
+        const GateKey k{gates[i].nq, gates[i].q[0], gates[i].nq == 2 ? gates[i].q[1] : -1, gates[i].flags};
+        if (!(k == plan->keys[(size_t)i])) fail(SV_ERR_PLAN, "gate " + std::to_string(i) + " differs from the planned list");
+    }
+    std::vector<unsigned char> host;
+    std::vector<BlockProg> progs;
+    const int seg_bits = (h->dtype == SV_C64 && plan->seg_bits == 5) ? 5 : 4;
+    if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
+    else build_programs<double>(plan, gates, seg_bits, host, progs);
+    upload_program(h, host);
+    const unsigned char *base = static_cast<const unsigned char *>(h->prog);
+    const uint64_t wait_ns = plan->wait_limit_ms > 0 ? (uint64_t)plan->wait_limit_ms * 1000000ull : kDefaultWaitNs;
+    size_t bi = 0;  // programs are in op order
+    for (int32_t oi = op_begin; oi < op_end; ++oi) {
+        const PlanOp &op = plan->ops[(size_t)oi];
+        if (op.kind == 2) {
+            while (bi < progs.size() && progs[bi].op_index < oi) ++bi;
+            if (bi == progs.size() || progs[bi].op_index != oi) fail(SV_ERR_PLAN, "no program for a blocking section");
+            const BlockProg &bp = progs[bi];
+            launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err, seg_bits,
+                         h->stream, wait_ns);
+        } else {
+            // pairs inside the piece; the others move data between pieces and are the caller's
+            std::vector<std::pair<int32_t, int32_t>> local;
+            for (const auto &pq : op.pairs)
+                if (pq.first < h->n && pq.second < h->n) local.push_back(pq);
+            if (!local.empty()) launch_permute(h->dtype, h->amp, h->n, local, h->stream);
+        }
+    }
+    SV_API_END
+}
+
+sv_status sv_shard_pack(sv_handle h, int32_t bit, int32_t value, void *dev_out) {
+    SV_API_BEGIN
+    if (!h || !dev_out) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    if (bit < 0) {
+        check_cuda(cudaMemcpyAsync(dev_out, h->amp, bytes, cudaMemcpyDeviceToDevice, h->stream), "cudaMemcpyAsync(pack)");
+    } else {
+        if (bit >= h->n || (value != 0 && value != 1)) fail(SV_ERR_ARG, "sv_shard_pack: bit or value out of range");
+        launch_shard_half(true, h->dtype, h->amp, h->n, bit, value, dev_out, h->stream);
+    }
+    SV_API_END
+}
+
+sv_status sv_shard_unpack(sv_handle h, int32_t bit, int32_t value, const void *dev_in) {
+    SV_API_BEGIN
+    if (!h || !dev_in) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    if (bit < 0) {
+        check_cuda(cudaMemcpyAsync(h->amp, dev_in, bytes, cudaMemcpyDeviceToDevice, h->stream), "cudaMemcpyAsync(unpack)");
+    } else {
+        if (bit >= h->n || (value != 0 && value != 1)) fail(SV_ERR_ARG, "sv_shard_unpack: bit or value out of range");
+        launch_shard_half(false, h->dtype, h->amp, h->n, bit, value, const_cast<void *>(dev_in), h->stream);
+    }
     SV_API_END
 }
 

@@ -231,6 +231,19 @@ struct Mat2d { double m[32]; };
 
 void launch_gate(int dtype, void *state, int n, const sv_gate &g, cudaStream_t st);
 void launch_init_basis(int dtype, void *state, int n, uint64_t basis, cudaStream_t st);
+// SIMT section programs of a contiguous-chunk plan, laid out as one device upload (api.cu).
+struct SimtPrograms {
+    struct Prog {
+        size_t off;
+        int nseg, ngate, op_index;
+    };
+    std::vector<unsigned char> host;
+    std::vector<Prog> progs;
+    int seg_bits = 4;
+};
+void build_simt_programs(const sv_plan *plan, const sv_gate *gates, int dtype, SimtPrograms &out);
+// Amplitudes with bit `bit` == value, in index order, to / from a buffer of 2^(n-1) (k_shard.cu).
+void launch_shard_half(bool pack, int dtype, void *state, int n, int bit, int value, void *buf, cudaStream_t st);
 
 struct PermPlan;  // defined in k_permute.cu
 void launch_permute(int dtype, void *state, int n, const std::vector<std::pair<int32_t, int32_t>> &pairs,
