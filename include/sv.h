@@ -123,6 +123,11 @@ sv_status sv_init_basis(sv_handle h, uint64_t basis_index);
  * Layout as sv_dtype.  Synchronous with respect to the host. */
 sv_status sv_get_state(sv_handle h, void *host_out);
 sv_status sv_set_state(sv_handle h, const void *host_in);
+/* The same copies, asynchronous on the handle's stream: host_out / host_in must be pinned host
+ * memory that stays valid (and, for host_in, unchanged) until the stream has passed the copy
+ * (sv_synchronize).  Copies on one handle's stream overlap kernels on another handle's stream. */
+sv_status sv_get_state_async(sv_handle h, void *host_out);
+sv_status sv_set_state_async(sv_handle h, const void *host_in);
 
 /* Device pointer of the amplitude array (borrowed; valid until sv_destroy). */
 sv_status sv_device_ptr(sv_handle h, void **dev_ptr);

@@ -145,6 +145,14 @@ class StateVector:
         ptr = host.ctypes.data if isinstance(host, np.ndarray) else host
         check(lib().sv_set_state(self._h, ptr))
 
+    def set_state_async(self, host_ptr: int) -> None:
+        """sv_set_state_async from pinned host memory at host_ptr (an integer address)."""
+        check(lib().sv_set_state_async(self._h, host_ptr))
+
+    def get_state_async(self, host_ptr: int) -> None:
+        """sv_get_state_async into pinned host memory at host_ptr."""
+        check(lib().sv_get_state_async(self._h, host_ptr))
+
     def device_ptr(self) -> int:
         p = ctypes.c_void_p()
         check(lib().sv_device_ptr(self._h, ctypes.byref(p)))

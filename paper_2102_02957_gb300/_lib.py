@@ -69,6 +69,8 @@ _SIGS = {
     "sv_destroy": (ctypes.c_int, [_VP]),
     "sv_init_basis": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sv_get_state": (ctypes.c_int, [_VP, _VP]),
+    "sv_get_state_async": (ctypes.c_int, [_VP, _VP]),
+    "sv_set_state_async": (ctypes.c_int, [_VP, _VP]),
     "sv_set_state": (ctypes.c_int, [_VP, _VP]),
     "sv_device_ptr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
     "sv_synchronize": (ctypes.c_int, [_VP]),

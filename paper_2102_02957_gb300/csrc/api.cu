@@ -383,6 +383,22 @@ sv_status sv_set_state(sv_handle h, const void *host_in) {
     SV_API_END
 }
 
+sv_status sv_get_state_async(sv_handle h, void *host_out) {
+    SV_API_BEGIN
+    if (!h || !host_out) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    check_cuda(cudaMemcpyAsync(host_out, h->amp, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync(D2H)");
+    SV_API_END
+}
+
+sv_status sv_set_state_async(sv_handle h, const void *host_in) {
+    SV_API_BEGIN
+    if (!h || !host_in) fail(SV_ERR_ARG, "null argument");
+    const size_t bytes = (size_t(1) << h->n) * amp_bytes(h->dtype);
+    check_cuda(cudaMemcpyAsync(h->amp, host_in, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync(H2D)");
+    SV_API_END
+}
+
 sv_status sv_device_ptr(sv_handle h, void **p) {
     SV_API_BEGIN
     if (!h || !p) fail(SV_ERR_ARG, "null argument");

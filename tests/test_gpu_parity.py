@@ -356,3 +356,32 @@ def test_diag_outside_sections(sv, dtype, n, c, pinned):
         ref = sim.simulate(n, desc, x)
         assert_close(_run(sv, n, desc, dtype, basis=x,
                           plan_opts=dict(chunk_bits=c, gather_pinned=pinned, diag_outside=1)), ref, dtype)
+
+
+def test_async_state_copies_on_two_streams(sv):
+    """sv_set_state_async / sv_get_state_async from and to pinned host memory, two states on two
+    streams taking turns (the benchmark's end-to-end pipeline), against the oracle."""
+    import torch
+    n, c = 20, 10
+    desc = cg.quantum_volume(n, 4, 31)
+    gates = sv.make_gates(desc)
+    plan = sv.Plan(n, gates, chunk_bits=c)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    states = [sv.StateVector(n, "c64", stream=s) for s in streams]
+    h_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()
+    h_in[5] = 1.0
+    h_out = [torch.zeros(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+    try:
+        for i in range(4):
+            k = i & 1
+            states[k].set_state_async(h_in.data_ptr())
+            states[k].apply(gates, plan)
+            states[k].get_state_async(h_out[k].data_ptr())
+        for s in states:
+            s.synchronize()
+        ref = sim.simulate(n, desc, 5)
+        for k in range(2):
+            assert_close(h_out[k].numpy(), ref, "c64")
+    finally:
+        for s in states:
+            s.close()
