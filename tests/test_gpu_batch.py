@@ -86,6 +86,19 @@ def test_batch_trajectory_mix_norms_and_sampled_parity(sv):
         assert_close(out[k], sim.simulate(ns[k], descs[k]), "c64")
 
 
+@pytest.mark.parametrize("use_tc", [0, 1])
+def test_batch_trajectories_up_to_24_qubits(sv, use_tc):
+    """Config 4's range at its top: depolarizing trajectories of the depth-30 random-layer circuit
+    (p = 1e-3) on 12..24 qubits, three of them 24-qubit, and two 20-qubit ansatz parameter sets,
+    one graph-replayed launch; every state against the oracle."""
+    sizes = [24, 23, 24, 22, 18, 12, 20, 24, 16, 21]
+    ns, descs = _workload(sizes, 30, 1e-3, 17, hea_n=20, hea_sets=2)
+    out, (items, sections, _) = _run_batch(sv, ns, descs, True, repeats=1, use_tc=use_tc)
+    assert sections > len(ns)
+    for n, d, got in zip(ns, descs, out):
+        assert_close(got, sim.simulate(n, d), "c64")
+
+
 def test_batch_rejects_unsupported(sv):
     g = sv.make_gates(cg.hea(8, 2, 1, 0))
     with sv.StateVector(8, "c128") as s:

@@ -138,3 +138,66 @@ def test_random_layers_33_complex128_mirror(sv):
         total = float(p.sum()) + p0
         del p
     assert abs(p0 - 1.0) <= 1e-11 and rest <= 1e-20 and abs(total - 1.0) <= 1e-11, (p0, rest, total)
+
+
+def _device_compare(a, b, piece=1 << 28):
+    """(max |a - b|, 1 - fidelity) of two complex64 CUDA tensors, in FP64 pieces."""
+    import torch
+    mx, ov, na, nb = 0.0, 0j, 0.0, 0.0
+    for s in range(0, a.numel(), piece):
+        x = a[s:s + piece].to(torch.complex128)
+        y = b[s:s + piece].to(torch.complex128)
+        mx = max(mx, float((x - y).abs().max()))
+        ov += complex(torch.vdot(y, x))
+        na += float(torch.vdot(x, x).real)
+        nb += float(torch.vdot(y, y).real)
+    return mx, 1.0 - abs(ov) ** 2 / (na * nb)
+
+
+@pytest.mark.parametrize("name", ["qv32", "rl32"])
+def test_config5_n32_complex64_tensor_cores(sv, name):
+    """Config 5 at n = 32, complex64 (32 GiB), on the benchmark's path (gathered chunks, tensor-core
+    groups, look-ahead chunk choice): the cache-blocked result against the per-gate path on the
+    device (two independent kernels), its FP64 norm, and the circuit followed by its inverse back
+    to |0..0>.  The oracle's own n = 32 run (64 GiB complex128, about 11 minutes of host time per
+    circuit) is not repeated here; at n = 30 it is (test above)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 80 * GIB:
+        pytest.skip("needs 80 GiB of free device memory")
+    w = cg.WORKLOADS[name]
+    n = w["n"]
+    pinned = w.get("pinned", 4)
+    desc = cg.build(name)
+    g = sv.make_gates(desc)
+    opts = dict(chunk_bits=w["c"], gather_pinned=pinned, use_tc=1, lookahead=1)
+    a = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    b = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    try:
+        with sv.StateVector(n, "c64", buffer=a) as st:
+            st.init_basis(0)
+            st.apply(g, sv.Plan(n, g, **opts))
+            norm = st.norm2()
+        with sv.StateVector(n, "c64", buffer=b) as st:
+            st.init_basis(0)
+            st.apply(g)  # per-gate path
+            st.synchronize()
+        torch.cuda.synchronize()
+        mx, inf = _device_compare(a, b)
+        print(f"{name}: blocked vs per-gate max-abs {mx:.3e}, 1-F {inf:.3e}, norm-1 {norm - 1:.3e}")
+        assert mx <= 1e-5 and inf <= 1e-8, (mx, inf)
+        assert abs(norm - 1.0) <= 1e-9
+        mirror = sv.make_gates(cg.mirror(desc))
+        with sv.StateVector(n, "c64", buffer=a) as st:
+            st.init_basis(0)
+            st.apply(mirror, sv.Plan(n, mirror, **opts))
+            st.synchronize()
+        torch.cuda.synchronize()
+        a0 = complex(a[0])
+        a[0] = 0
+        rest = float(a.abs().max())
+        print(f"{name} mirror: amplitude 0 = {a0:.9f}, largest other {rest:.3e}")
+        assert abs(a0 - 1.0) <= 1e-5 and rest <= 1e-5
+    finally:
+        del a, b
+        torch.cuda.empty_cache()
