@@ -70,38 +70,44 @@ __device__ __forceinline__ void gather_coords(const GatherArgs &ga, int64_t x, i
     for (int d = ga.rank; d < 5; ++d) coord[d] = 0;
 }
 
-// Producer (one thread): stream this CTA's chunks j = blockIdx.x + it * gridDim.x into the ring
+// Producer (one warp): stream this CTA's chunks j = blockIdx.x + it * gridDim.x into the ring
 // of nbuf shared-memory buffers (bulk copies for contiguous chunks, tensor copies for gathered
-// ones), each completing on full[slot]; a slot is reused once the store thread released it on
-// empty[slot].
+// ones), each completing on full[slot]; a slot is reused once the store warp released it on
+// empty[slot].  A gathered chunk with more runs of bits than a tensor map has dimensions takes
+// several boxes; each lane issues its own, since one thread issuing them in sequence waits on
+// every box in turn.
 template <typename T2>
 __device__ __forceinline__ void produce_chunks(T2 *state, int c, int64_t count, int nbuf, T2 *bufs, uint64_t *full,
                                                uint64_t *empty, volatile int *abort_flag, int *err,
                                                const GatherArgs &ga, const CUtensorMap *tmap, uint64_t wait_ns) {
+    const int lane = threadIdx.x & 31;
     const int chunk_amps = 1 << c;
     const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
     int64_t issued = 0;
     for (int64_t it = 0; it < count; ++it) {
         const int s = (int)(it % nbuf);
-        if (it >= nbuf) {
-            if (!ptx::mbar_wait(&empty[s], (uint32_t)((it / nbuf - 1) & 1), wait_ns) || *abort_flag) {
+        bool ok = true;
+        if (it >= nbuf) ok = ptx::mbar_wait(&empty[s], (uint32_t)((it / nbuf - 1) & 1), wait_ns) && !*abort_flag;
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
                 atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
                 *abort_flag = 1;
-                break;
             }
+            break;
         }
         const int64_t j = blockIdx.x + it * gridDim.x;
         unsigned char *dst = reinterpret_cast<unsigned char *>(bufs + (size_t)s * chunk_amps);
-        ptx::mbar_arrive_expect_tx(&full[s], chunk_bytes);
+        if (lane == 0) ptx::mbar_arrive_expect_tx(&full[s], chunk_bytes);
+        __syncwarp();
         if (ga.rank > 0) {
-            for (int t = 0; t < (1 << ga.nloop); ++t) {
+            for (int t = lane; t < (1 << ga.nloop); t += 32) {
                 int coord[5];
                 gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
                 ptx::tensor_g2s(dst + (size_t)t * ga.box_amps * sizeof(T2), tmap, coord, ga.rank, &full[s]);
             }
         } else {
             const unsigned char *src = reinterpret_cast<const unsigned char *>(state + j * chunk_amps);
-            for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+            for (uint32_t o = (uint32_t)lane * kPiece; o < chunk_bytes; o += 32u * kPiece) {
                 const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
                 ptx::bulk_g2s(dst + o, src + o, b, &full[s]);
             }
@@ -113,29 +119,30 @@ __device__ __forceinline__ void produce_chunks(T2 *state, int c, int64_t count, 
         (void)ptx::mbar_wait(&full[it % nbuf], (uint32_t)((it / nbuf) & 1), wait_ns);
 }
 
-// Issue the copies that write chunk j back from shared memory (one thread).
+// Issue the copies that write chunk j back from shared memory (lane `lane` of the store warp
+// takes every 32nd box or piece).
 template <typename T2>
 __device__ __forceinline__ void write_chunk(T2 *state, int c, int64_t j, const T2 *buf, const GatherArgs &ga,
-                                            const CUtensorMap *tmap) {
+                                            const CUtensorMap *tmap, int lane) {
     const int chunk_amps = 1 << c;
     const uint32_t chunk_bytes = (uint32_t)chunk_amps * (uint32_t)sizeof(T2);
     const unsigned char *srcs = reinterpret_cast<const unsigned char *>(buf);
     if (ga.rank > 0) {
-        for (int t = 0; t < (1 << ga.nloop); ++t) {
+        for (int t = lane; t < (1 << ga.nloop); t += 32) {
             int coord[5];
             gather_coords<T2>(ga, gather_origin(ga, j, t), coord);
             ptx::tensor_s2g(tmap, coord, ga.rank, srcs + (size_t)t * ga.box_amps * sizeof(T2));
         }
     } else {
         unsigned char *dstg = reinterpret_cast<unsigned char *>(state + j * chunk_amps);
-        for (uint32_t o = 0; o < chunk_bytes; o += kPiece) {
+        for (uint32_t o = (uint32_t)lane * kPiece; o < chunk_bytes; o += 32u * kPiece) {
             const uint32_t b = chunk_bytes - o < (uint32_t)kPiece ? chunk_bytes - o : (uint32_t)kPiece;
             ptx::bulk_s2g(dstg + o, srcs + o, b);
         }
     }
 }
 
-// Store thread: write the CTA's chunks back in order as their consumers finish them (done[slot])
+// Store warp: write the CTA's chunks back in order as their consumers finish them (done[slot])
 // and release each slot to the producer (empty[slot]) as soon as the copies have read it.
 // (Keeping two write-backs in flight, releasing chunk it - 1 after chunk it's copies are issued,
 // was measured slower: the slot is held longer and the prefetch depth shrinks.)
@@ -143,19 +150,24 @@ template <typename T2>
 __device__ __forceinline__ void store_chunks(T2 *state, int c, int64_t count, int nbuf, const T2 *bufs, uint64_t *done,
                                              uint64_t *empty, volatile int *abort_flag, int *err,
                                              const GatherArgs &ga, const CUtensorMap *tmap, uint64_t wait_ns) {
+    const int lane = threadIdx.x & 31;
     const int chunk_amps = 1 << c;
     for (int64_t it = 0; it < count; ++it) {
         const int s = (int)(it % nbuf);
         // use it / nbuf of done[s]: the previous use (chunk it - nbuf) was waited for here
-        if (!ptx::mbar_wait(&done[s], (uint32_t)((it / nbuf) & 1), wait_ns) || *abort_flag) {
-            atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
-            *abort_flag = 1;
+        const bool ok = ptx::mbar_wait(&done[s], (uint32_t)((it / nbuf) & 1), wait_ns) && !*abort_flag;
+        if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) {
+                atomicCAS(err, DEV_OK, DEV_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
             break;
         }
-        write_chunk<T2>(state, c, blockIdx.x + it * gridDim.x, bufs + (size_t)s * chunk_amps, ga, tmap);
+        write_chunk<T2>(state, c, blockIdx.x + it * gridDim.x, bufs + (size_t)s * chunk_amps, ga, tmap, lane);
         ptx::bulk_commit();
         ptx::bulk_wait_read<0>();
-        ptx::mbar_arrive(&empty[s]);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&empty[s]);
     }
     ptx::bulk_wait<0>();
 }
@@ -222,9 +234,9 @@ __device__ __forceinline__ void block_body(typename V2<T>::type *__restrict__ st
 
     if (threadIdx.x < kSvcThreads) {
         // ------------------------------------------------- producer (warp 0), store (warp 1)
-        if (threadIdx.x == 0)
+        if (threadIdx.x < 32)
             produce_chunks<T2>(state, c, count, nbuf, bufs, full, empty, abort_flag, err, ga, &tmap, wait_ns);
-        else if (threadIdx.x == 32)
+        else
             store_chunks<T2>(state, c, count, nbuf, bufs, done, empty, abort_flag, err, ga, &tmap, wait_ns);
         return;
     }
