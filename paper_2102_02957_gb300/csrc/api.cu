@@ -442,7 +442,7 @@ sv_status sv_plan_get_info(sv_plan_h p, sv_plan_info *info) {
         if (op.kind == 2 || op.kind == 4) { ++info->n_blocks; info->n_gates_emitted += (int64_t)op.gates.size(); }
         if (op.kind == 3) ++info->n_unpermute_rounds;
     }
-    info->n_segments = p->n_segments;
+    info->n_segments = plan_segment_count(*p);
     for (int q = 0; q < p->n && q < 64; ++q) info->final_map[q] = p->final_map[q];
     SV_API_END
 }

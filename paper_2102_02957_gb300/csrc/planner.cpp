@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include "sv_internal.h"
 
@@ -319,99 +320,204 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         plan->final_map = src;
     }
 
-    // register groups per block (for statistics and execution)
-    int nseg = 0;
-    for (const PlanOp &op : plan->ops) {
-        if (op.kind == 2)
-            nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), plan->seg_bits, 8).size();
-        if (op.kind == 4) {
-            const GatherLayout L = gather_layout(op.mask, n, 8);
-            nseg += (int)segment_block(localize_gates(op, n, c, &L), L.ce, plan->seg_bits, 8).size();
-        }
-    }
-    plan->n_segments = nseg;
     return plan;
 }
 
 // ---------------------------------------------------------------------------------------
 // Register groups.  Inside a blocking section each chunk lives in shared memory; a group is
 // a set of r chunk bits whose 2^r amplitudes one thread holds in registers while it applies
-// every gate of the group.  The group's bits start from the first pending gate's and grow by
-// look-ahead (the pending gate whose new bits let the group take the most gates); the group then
-// takes, in section order, every gate inside its bits, and a gate that is not taken blocks its
-// bits for the rest of the group (so per-qubit gate order is kept) -- the transpiler's
-// QB_BLOCKED rule one level down.
+// every gate of the group.  A group on bits S takes, in section order, every pending gate inside
+// S, and a gate that is not taken blocks its bits for the rest of the group (so per-qubit gate
+// order is kept) -- the transpiler's QB_BLOCKED rule one level down.  Each group costs the
+// section one pass over its chunk, so the groups are chosen to be few: a beam search over the
+// pending gate lists (beam_groups below); a group is an r-subset of the bits the pending gates
+// use (a superset of bits takes a superset of the gates, so r-subsets suffice).  A section whose
+// search exceeds its budget falls back to the greedy choice: the first pending gate's bits,
+// grown one pending gate at a time (the first 64 with new bits) by the one that lets the group
+// take the most gates.
 //
 // Lane layout: the lanes that share a shared-memory wavefront (16 for 8-byte amplitudes, 8 for
 // 16-byte ones) must enumerate distinct bank slots.  A chunk bit k contributes the slot vector
 // w(k) = 2^k for k < SB and the swizzle pattern V[k] above; the first lane bits are chosen
 // greedily (ascending bit order) among the bits outside the group so that their w(k) are
 // linearly independent over GF(2).
+namespace {
+
+// Gates of `pending` a group on `bits` takes (in order) and the rest.
+void split_pending(const std::vector<uint64_t> &mask, const std::vector<int32_t> &pending, uint64_t bits,
+                   std::vector<int32_t> *taken, std::vector<int32_t> &rest) {
+    uint64_t blocked = 0;
+    rest.clear();
+    for (int32_t idx : pending) {
+        const uint64_t mk = mask[idx];
+        if ((mk & ~bits) == 0 && (mk & blocked) == 0) {
+            if (taken) taken->push_back(idx);
+        } else {
+            blocked |= mk;
+            rest.push_back(idx);
+        }
+    }
+}
+
+struct VecHash {
+    size_t operator()(const std::vector<int32_t> &v) const {
+        uint64_t h = 1469598103934665603ull;
+        for (int32_t x : v) h = (h ^ (uint64_t)(uint32_t)x) * 1099511628211ull;
+        return (size_t)h;
+    }
+};
+
+// Groups by beam search: level by level, every r-subset of the bits the pending gates use is
+// tried on each of the kGroupBeam pending lists kept (subsets in lexicographic order of their bit
+// positions); the children are ranked by the lower bound ceil(|bits used| / r) on the groups they
+// still need, then by pending gates, then by bits used (stable: ties keep the order they were
+// found in), and the first list to empty ends the search.  Returns false once the budget of
+// pending-gate visits is spent.
+constexpr int kGroupBeam = 8;
+constexpr int64_t kGroupSearchBudget = 4000000;  // pending-gate visits per section
+
+bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out) {
+    struct Node {
+        std::vector<int32_t> pend;
+        std::vector<uint64_t> sets;
+    };
+    auto used_of = [&](const std::vector<int32_t> &pend) {
+        uint64_t u = 0;
+        for (int32_t idx : pend) u |= mask[idx];
+        return u;
+    };
+    std::vector<Node> beam(1);
+    beam[0].pend.resize(mask.size());
+    std::iota(beam[0].pend.begin(), beam[0].pend.end(), 0);
+    if (beam[0].pend.empty()) return true;
+    int64_t budget = kGroupSearchBudget;
+    std::vector<int32_t> rest;
+    while (true) {
+        struct Child {
+            Node node;
+            int lb, npend, nbits;
+        };
+        std::vector<Child> children;
+        std::unordered_map<std::vector<int32_t>, int, VecHash> seen;
+        for (const Node &nd : beam) {
+            const uint64_t used = used_of(nd.pend);
+            if (popc(used) <= r) {  // one more group takes every pending gate
+                out = nd.sets;
+                out.push_back(used);
+                return true;
+            }
+            int bits[64], nb = 0;
+            for (int b = 0; b < 64; ++b)
+                if ((used >> b) & 1) bits[nb++] = b;
+            int sel[8];
+            for (int k = 0; k < r; ++k) sel[k] = k;
+            while (true) {
+                budget -= (int64_t)nd.pend.size();
+                if (budget < 0) return false;
+                uint64_t set = 0;
+                for (int k = 0; k < r; ++k) set |= 1ull << bits[sel[k]];
+                split_pending(mask, nd.pend, set, nullptr, rest);
+                if (rest.empty()) {
+                    out = nd.sets;
+                    out.push_back(set);
+                    return true;
+                }
+                if (rest.size() < nd.pend.size() && seen.emplace(rest, 0).second) {
+                    Child ch;
+                    ch.node.pend = rest;
+                    ch.node.sets = nd.sets;
+                    ch.node.sets.push_back(set);
+                    ch.nbits = popc(used_of(rest));
+                    ch.lb = (ch.nbits + r - 1) / r;
+                    ch.npend = (int)rest.size();
+                    children.push_back(std::move(ch));
+                }
+                // next r-subset of [0, nb) in lexicographic order
+                int k = r - 1;
+                while (k >= 0 && sel[k] == nb - r + k) --k;
+                if (k < 0) break;
+                ++sel[k];
+                for (int q = k + 1; q < r; ++q) sel[q] = sel[q - 1] + 1;
+            }
+        }
+        std::stable_sort(children.begin(), children.end(), [](const Child &a, const Child &b) {
+            if (a.lb != b.lb) return a.lb < b.lb;
+            if (a.npend != b.npend) return a.npend < b.npend;
+            return a.nbits < b.nbits;
+        });
+        if (children.size() > (size_t)kGroupBeam) children.resize(kGroupBeam);
+        beam.clear();
+        for (Child &c : children) beam.push_back(std::move(c.node));
+    }
+}
+
+}  // namespace
+
 std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes) {
     std::vector<HostSeg> segs;
     std::vector<int32_t> pending(gates.size());
     std::iota(pending.begin(), pending.end(), 0);
-    auto mask_of = [&](const BlockGate &g) {  // chunk bits only (a qubit outside has phys -1)
+    std::vector<uint64_t> mask(gates.size());  // chunk bits only (a qubit outside has phys -1)
+    for (size_t i = 0; i < gates.size(); ++i) {
         uint64_t mk = 0;
-        for (int j = 0; j < g.nq; ++j)
-            if (g.phys[j] >= 0) mk |= 1ull << g.phys[j];
-        return mk;
-    };
+        for (int j = 0; j < gates[i].nq; ++j)
+            if (gates[i].phys[j] >= 0) mk |= 1ull << gates[i].phys[j];
+        mask[i] = mk;
+    }
     const int rr = std::min(r, width);
-    // a gate with no chunk bit (a diagonal wholly outside the chunk) fits every group
-    bool any_outside = false;
-    for (const BlockGate &g : gates) any_outside = any_outside || mask_of(g) == 0;
-    // gates a group on `bits` takes: in order, those inside `bits` and not behind a deferred gate
-    // (once all of `bits` are blocked no later gate fits, unless it has no chunk bit)
-    auto takes = [&](uint64_t bits) {
-        uint64_t blocked = 0;
-        int k = 0;
-        for (int32_t idx : pending) {
-            const uint64_t mk = mask_of(gates[idx]);
-            if ((mk & ~bits) == 0 && (mk & blocked) == 0) {
-                ++k;
-            } else {
-                blocked |= mk;
-                if (!any_outside && (blocked & bits) == bits) break;
-            }
-        }
-        return k;
-    };
-    std::vector<int32_t> rest;
-    while (!pending.empty()) {
-        // the group's bits: the first pending gate's, then, one pending gate at a time (the first
-        // 64 with new bits), those that let the group take the most gates
-        uint64_t set = mask_of(gates[pending.front()]);
-        while (popc(set) < rr) {
-            uint64_t best = 0;
-            int best_k = -1;
-            size_t tried = 0;
-            for (size_t i = 0; i < pending.size() && tried < 64; ++i) {
-                const uint64_t fresh = mask_of(gates[pending[i]]) & ~set;
-                if (!fresh || popc(set | fresh) > rr) continue;
-                ++tried;
-                const int k = takes(set | fresh);
-                if (k > best_k) {
-                    best_k = k;
-                    best = fresh;
+    // the group sets: the search's, else the greedy choice
+    std::vector<uint64_t> sets;
+    if (!beam_groups(mask, rr, sets)) sets.clear();
+    if (sets.empty() && !pending.empty()) {
+        // a gate with no chunk bit (a diagonal wholly outside the chunk) fits every group
+        bool any_outside = false;
+        for (uint64_t mk : mask) any_outside = any_outside || mk == 0;
+        std::vector<int32_t> pend = pending, rest;
+        // gates a group on `bits` takes: in order, those inside `bits` and not behind a deferred
+        // gate (once all of `bits` are blocked no later gate fits, unless it has no chunk bit)
+        auto takes = [&](uint64_t bits) {
+            uint64_t blocked = 0;
+            int k = 0;
+            for (int32_t idx : pend) {
+                const uint64_t mk = mask[idx];
+                if ((mk & ~bits) == 0 && (mk & blocked) == 0) {
+                    ++k;
+                } else {
+                    blocked |= mk;
+                    if (!any_outside && (blocked & bits) == bits) break;
                 }
             }
-            if (!best) break;
-            set |= best;
+            return k;
+        };
+        while (!pend.empty()) {
+            uint64_t set = mask[pend.front()];
+            while (popc(set) < rr) {
+                uint64_t best = 0;
+                int best_k = -1;
+                size_t tried = 0;
+                for (size_t i = 0; i < pend.size() && tried < 64; ++i) {
+                    const uint64_t fresh = mask[pend[i]] & ~set;
+                    if (!fresh || popc(set | fresh) > rr) continue;
+                    ++tried;
+                    const int k = takes(set | fresh);
+                    if (k > best_k) {
+                        best_k = k;
+                        best = fresh;
+                    }
+                }
+                if (!best) break;
+                set |= best;
+            }
+            sets.push_back(set);
+            split_pending(mask, pend, set, nullptr, rest);
+            pend.swap(rest);
         }
-        uint64_t blocked = 0;
+    }
+    std::vector<int32_t> rest;
+    for (uint64_t set : sets) {
         HostSeg s;
         s.r = rr;
-        rest.clear();
-        for (int32_t idx : pending) {
-            const uint64_t mk = mask_of(gates[idx]);
-            if ((mk & ~set) == 0 && (mk & blocked) == 0) {
-                s.gates.push_back(idx);
-            } else {
-                blocked |= mk;
-                rest.push_back(idx);
-            }
-        }
+        split_pending(mask, pending, set, &s.gates, rest);
         // pad with the highest unused chunk bits (keeps the low bits free for the lanes)
         for (int p = width - 1; p >= 0 && popc(set) < rr; --p)
             if (!((set >> p) & 1)) set |= 1ull << p;
@@ -645,6 +751,22 @@ void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevG
         out.op = OP_DENSE2;
         for (int i = 0; i < 32; ++i) out.m[i] = (T)mm[i];
     }
+}
+
+// Register groups over all blocking sections of a plan (statistics; the same groups the section
+// programs get).
+int plan_segment_count(const sv_plan &plan) {
+    int nseg = 0;
+    const int n = plan.n, c = plan.c;
+    for (const PlanOp &op : plan.ops) {
+        if (op.kind == 2)
+            nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), plan.seg_bits, 8).size();
+        if (op.kind == 4) {
+            const GatherLayout L = gather_layout(op.mask, n, 8);
+            nseg += (int)segment_block(localize_gates(op, n, c, &L), L.ce, plan.seg_bits, 8).size();
+        }
+    }
+    return nseg;
 }
 
 // A gate that costs no multiplication-heavy work: diagonal, or a permutation (entries 0 / 1).

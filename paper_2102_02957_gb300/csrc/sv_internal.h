@@ -57,7 +57,6 @@ struct sv_plan {
     std::vector<sv::PlanOp> ops;
     std::vector<int32_t> final_map;
     std::vector<sv::GateKey> keys;  // structure of the gate list it was made from
-    int32_t n_segments = 0;
 };
 
 namespace sv {
@@ -143,6 +142,7 @@ struct HostSeg {
 // Split a section's gates (physical bits < width) into register groups of at most r bits,
 // and choose each group's lane layout for elements of elem_bytes bytes.
 std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes);
+int plan_segment_count(const sv_plan &plan);
 
 template <typename T>
 void encode_gate(const sv_gate &g, const BlockGate &bg, const HostSeg &seg, DevGate<T> &out);
