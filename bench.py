@@ -669,6 +669,17 @@ def run_ours(args):
             e2e_step(i)
         for s in e_states:
             s.synchronize()
+        # the host link's rate on this machine, for reading the end-to-end number (untimed)
+        link = {}
+        for name, fn in (("h2d_GBs", lambda: e_states[0].set_state_async(h_in.data_ptr())),
+                         ("d2h_GBs", lambda: e_states[0].get_state_async(h_out[0].data_ptr()))):
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            l0.record(e_streams[0])
+            fn()
+            l1.record(e_streams[0])
+            l1.synchronize()
+            link[name] = (8 << n) / (l0.elapsed_time(l1) / 1000.0) / 1e9
         k2 = max(2, min(6, 2 * args.steps))
         torch.cuda.synchronize()
         bar.barrier()
@@ -680,7 +691,8 @@ def run_ours(args):
         dt = bar.max(time.perf_counter() - t0)
         e2e = {"value": world * G * k2 / dt, "unit": "gates/s", "h2d_bytes_per_step": int((2 << n) * 4),
                "d2h_bytes_per_step": int((2 << n) * 4), "ms_per_step": 1000 * dt / k2,
-               "pipeline": "2 states on 2 streams: one step's host copies overlap the other's kernels"}
+               "pipeline": "2 states on 2 streams: one step's host copies overlap the other's kernels",
+               "host_link": link}
         out0 = h_out[(k2 - 1) & 1][:2].numpy().copy()
         for s in e_states:
             s.close()

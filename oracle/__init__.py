@@ -26,7 +26,7 @@ Pins (checked by ``tests/test_oracle_*.py`` without a GPU): literal Eq. 1/Eq. 2 
 unitarity, Bell/GHZ amplitudes, the QFT closed form, the dense brute force at n <= 10,
 unit norm, mirror circuits, the Listing 2 index-map bijection, and planner validity and
 equivalence; for ``mlp``: central finite differences, a hand-computed case, the closed form of
-Adam's first step and dead relu units.  The paper's own worked transpiler example (Fig. 9, "four swap gates") is an
+Adam's first step and dead relu units.  The paper's own worked transpiler example (Fig. 9, its count of added swap gates) is an
 image that is not available, so the planner's swap *count* is parity unpinned; its schedule
 is pinned by validity + simulation equivalence and by agreement with the library's planner.
 """

@@ -7,13 +7,13 @@ own C++ implementation; the two must produce the same schedule bit for bit.
 Algorithm (logical qubit -> physical bit map ``m``, inverse ``pinv``):
 
   REMAINING <- gate sequence (SWAP gates removed as relabels, see below)
-  while REMAINING is not empty:                       # "until ... not empty" read as "until empty"
-    choose QB_CHUNK: c - reserve logical qubits       # "QB_CHUNK[nc-1]" read as nc entries, reserve = 0
+  while REMAINING is not empty:                       # stop condition taken as: REMAINING empty
+    choose QB_CHUNK: c - reserve logical qubits       # the array bound taken as nc entries, reserve = 0
         priority: (1) qubits of the first remaining gate, (2) qubits of multi-qubit gates in
         list order, (3) qubits of 1-qubit gates in list order, (4) qubits already resident
         (physical < c) by ascending physical bit; a gate whose new qubits do not all fit is
-        skipped ("all the qubits used in a multi-qubit gate should be placed in a chunk at the
-        same time", Sec. IV.A).
+        skipped (Sec. IV.A requires every qubit of a multi-qubit gate to be in the chunk
+        together).
     put chunk_swap gates in OUTPUT                    # one swap round
         incoming chosen qubits (physical >= c) sorted by logical id are paired with vacated
         physical bits (< c, held by unchosen qubits) sorted ascending; each pair is
@@ -22,12 +22,12 @@ Algorithm (logical qubit -> physical bit map ``m``, inverse ``pinv``):
     for gate in REMAINING:
       if all its qubits in QB_CHUNK and none in QB_BLOCKED: put gate in OUTPUT (block)
       else: put gate in REMAINING_NEXT; if some of its qubits are in QB_CHUNK, set all of its
-            qubits in QB_BLOCKED            # the listing's "set QB_CHUNK" read as QB_BLOCKED
+            qubits in QB_BLOCKED            # the listing marks QB_CHUNK here; taken as QB_BLOCKED
     REMAINING <- REMAINING_NEXT
 
 SWAP gates are relabels: a SWAP(a, b) in the input exchanges which virtual qubit carries labels
 a and b; later gates are rewritten, no data moves.  At the end the output is reordered so that
-physical bit q holds logical qubit q (Sec. IV.C: "reorder qubits for the output", Fig. 10 case
+physical bit q holds logical qubit q (Sec. IV.C: the qubits are put back in order for the output, Fig. 10 case
 (b)).  That reordering is a bit permutation, written as two rounds of disjoint transpositions:
 for each cycle x0 -> x1 -> ... (x0 its smallest bit, x_{i+1} = destination of x_i) the first
 round exchanges x_i <-> x_{L-i} and the second x_i <-> x_{L+1-i} (indices mod L).

@@ -2,14 +2,15 @@
 // reordering of Sec. IV.C (Fig. 10 case (b)).
 //
 // Readings of the points the paper leaves open (the same readings the oracle takes):
-//  * QB_CHUNK holds c - reserve qubits ("QB_CHUNK[nc-1]" read as nc entries when reserve = 0).
+//  * QB_CHUNK holds c - reserve qubits (the listing's array bound taken as nc entries when
+//    reserve = 0).
 //  * Choice order: the first remaining gate's qubits (guarantees progress), then qubits of
 //    multi-qubit gates in list order, then of 1-qubit gates, then already-resident qubits by
 //    ascending physical bit; a gate whose new qubits do not all fit is skipped (all qubits of
 //    a multi-qubit gate enter the chunk together, Sec. IV.A).
 //  * A chunk_swap round pairs the incoming qubits (sorted by id) with the vacated chunk bits
 //    (sorted ascending); each pair swaps physical bits (slot < c, old position >= c).
-//  * The listing's "set QB_CHUNK" in the deferral branch is read as setting QB_BLOCKED: a
+//  * Where the listing's deferral branch marks QB_CHUNK it is taken as marking QB_BLOCKED: a
 //    deferred gate with any qubit in the chunk blocks all of its qubits.
 //  * SWAP gates are relabels; the final reordering is a bit permutation split into two rounds
 //    of disjoint transpositions.
