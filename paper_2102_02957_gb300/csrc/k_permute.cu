@@ -19,9 +19,8 @@ namespace sv {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnitsPerCta = 1024;  // 16-byte units per side staged in shared memory
+constexpr int kUnitsPerCta = 512;   // 16-byte units per side and batch staged in shared memory
 constexpr int kMaxItems = 128;      // outer items per batch (tiles are at least 8 units)
-constexpr int kLoadsPerThread = kUnitsPerCta / kThreads;
 
 struct PermArgs {
     int vbits;        // |V|
@@ -41,20 +40,44 @@ __device__ __forceinline__ int64_t insert0(int64_t x, int p) {
     return ((x >> p) << (p + 1)) | low;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Byte offset of tile unit ut (its first amplitude v0 = ut * apu in V coordinates) from the tile
+// base: the low bits stay, the extra V bits are deposited at their physical positions.
+__device__ __forceinline__ int64_t unit_offset(const PermArgs &P, int v0) {
+    int64_t off = v0 & ((1 << P.L0) - 1);
+    for (int j = 0; j < P.nextra; ++j) off |= int64_t((v0 >> (P.L0 + j)) & 1) << P.vpos[P.L0 + j];
+    return off;
+}
+
+// Batches b = blockIdx.x, + gridDim.x, ... in two shared-memory buffers: while batch b is
+// permuted and written back from one buffer, batch b + gridDim.x is already in flight into the
+// other (cp.async), so loads and stores overlap.  The grid is 32 times the resident CTAs:
+// batches differ in work (pairs whose partner comes first are skipped), and many short-lived
+// CTAs keep the SMs evenly loaded (measured: 3.55 ms per n = 30 pass against 4.78 ms with one
+// wave of persistent CTAs and 5.92 ms with one buffer).
 template <typename T2>
-__global__ void __launch_bounds__(kThreads, 4) k_permute(T2 *a, PermArgs P) {
+__global__ void __launch_bounds__(kThreads, 6) k_permute(T2 *a, PermArgs P) {
     constexpr int apu = 16 / sizeof(T2);  // amplitudes per 16-byte unit
-    __shared__ __align__(16) T2 sA[kUnitsPerCta * apu];
-    __shared__ __align__(16) T2 sB[kUnitsPerCta * apu];
-    __shared__ int64_t s_base[kMaxItems], s_base2[kMaxItems];
-    __shared__ int s_mode[kMaxItems];  // 0 skip, 1 self, 2 exchange
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2 *sA = reinterpret_cast<T2 *>(smem);            // [2][kUnitsPerCta * apu]
+    T2 *sB = sA + 2 * kUnitsPerCta * apu;             // [2][kUnitsPerCta * apu]
+    __shared__ int64_t s_base[2][kMaxItems], s_base2[2][kMaxItems];
+    __shared__ int s_mode[2][kMaxItems];  // 0 skip, 1 self, 2 exchange
 
     const int T = 1 << P.vbits;
     const int lg_upt = P.vbits - (apu == 2 ? 1 : 0);
     const int upt = 1 << lg_upt;  // units per tile (T / apu)
+    const int units = P.ib * upt;
     const int64_t nbatch = (P.nitems + P.ib - 1) / P.ib;
 
-    for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    // items of batch `batch` into slot k (threads < ib), then (after a barrier) its loads
+    auto describe = [&](int64_t batch, int k) {
         for (int it = threadIdx.x; it < P.ib; it += kThreads) {
             const int64_t o = batch * P.ib + it;
             int mode = 0;
@@ -71,49 +94,48 @@ __global__ void __launch_bounds__(kThreads, 4) k_permute(T2 *a, PermArgs P) {
                 if (base2 > base) mode = 2;
                 else if (base2 == base && P.nlow > 0) mode = 1;
             }
-            s_base[it] = base;
-            s_base2[it] = base2;
-            s_mode[it] = mode;
+            s_base[k][it] = base;
+            s_base2[k][it] = base2;
+            s_mode[k][it] = mode;
         }
-        __syncthreads();
-
-        // every unit of this thread is loaded into registers before any is staged, so that all of
-        // its loads are in flight at once (a batch has at most kUnitsPerCta = kLoadsPerThread *
-        // kThreads units per side)
-        const int units = P.ib * upt;
-        uint4 xs[kLoadsPerThread], ys[kLoadsPerThread];
-#pragma unroll
-        for (int k = 0; k < kLoadsPerThread; ++k) {
-            const int u = threadIdx.x + k * kThreads;
-            if (u >= units) continue;
-            const int it = u >> lg_upt, ut = u & (upt - 1);
-            const int mode = s_mode[it];
-            if (!mode) continue;
-            const int v0 = ut * apu;
-            int64_t off = v0 & ((1 << P.L0) - 1);
-            for (int j = 0; j < P.nextra; ++j) off |= int64_t((v0 >> (P.L0 + j)) & 1) << P.vpos[P.L0 + j];
-            xs[k] = *reinterpret_cast<const uint4 *>(a + s_base[it] + off);
-            if (mode == 2) ys[k] = *reinterpret_cast<const uint4 *>(a + s_base2[it] + off);
-        }
-#pragma unroll
-        for (int k = 0; k < kLoadsPerThread; ++k) {
-            const int u = threadIdx.x + k * kThreads;
-            if (u >= units) continue;
-            const int it = u >> lg_upt;
-            const int mode = s_mode[it];
-            if (!mode) continue;
-            *reinterpret_cast<uint4 *>(sA + (size_t)u * apu) = xs[k];
-            if (mode == 2) *reinterpret_cast<uint4 *>(sB + (size_t)u * apu) = ys[k];
-        }
-        __syncthreads();
-
+    };
+    auto load = [&](int k) {
+        const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(sA + (size_t)k * kUnitsPerCta * apu);
+        const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(sB + (size_t)k * kUnitsPerCta * apu);
         for (int u = threadIdx.x; u < units; u += kThreads) {
             const int it = u >> lg_upt, ut = u & (upt - 1);
-            const int mode = s_mode[it];
+            const int mode = s_mode[k][it];
+            if (!mode) continue;
+            const int64_t off = unit_offset(P, ut * apu);
+            cp_async16(a0 + (uint32_t)u * 16u, a + s_base[k][it] + off);
+            if (mode == 2) cp_async16(b0 + (uint32_t)u * 16u, a + s_base2[k][it] + off);
+        }
+    };
+
+    int64_t batch = blockIdx.x;
+    if (batch < nbatch) {
+        describe(batch, 0);
+        __syncthreads();
+        load(0);
+    }
+    cp_async_commit();
+    for (int k = 0; batch < nbatch; batch += gridDim.x, k ^= 1) {
+        const int64_t next = batch + gridDim.x;
+        if (next < nbatch) {
+            describe(next, k ^ 1);
+            __syncthreads();
+            load(k ^ 1);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // this batch's copies (the next one's may still be in flight)
+        __syncthreads();
+        const T2 *A = sA + (size_t)k * kUnitsPerCta * apu, *B = sB + (size_t)k * kUnitsPerCta * apu;
+        for (int u = threadIdx.x; u < units; u += kThreads) {
+            const int it = u >> lg_upt, ut = u & (upt - 1);
+            const int mode = s_mode[k][it];
             if (!mode) continue;
             const int v0 = ut * apu;
-            int64_t off = v0 & ((1 << P.L0) - 1);
-            for (int j = 0; j < P.nextra; ++j) off |= int64_t((v0 >> (P.L0 + j)) & 1) << P.vpos[P.L0 + j];
+            const int64_t off = unit_offset(P, v0);
             T2 outA[apu], outB[apu];
 #pragma unroll
             for (int e = 0; e < apu; ++e) {
@@ -123,14 +145,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_permute(T2 *a, PermArgs P) {
                     v ^= (d << P.lp[j]) | (d << P.lq[j]);
                 }
                 const size_t src = (size_t)it * T + v;
-                outA[e] = mode == 2 ? sB[src] : sA[src];  // a'[(o, v)]  = a[(o', P_low(v))]
-                outB[e] = sA[src];                        // a'[(o', v)] = a[(o, P_low(v))]
+                outA[e] = mode == 2 ? B[src] : A[src];  // a'[(o, v)]  = a[(o', P_low(v))]
+                outB[e] = A[src];                       // a'[(o', v)] = a[(o, P_low(v))]
             }
-            *reinterpret_cast<uint4 *>(a + s_base[it] + off) = *reinterpret_cast<const uint4 *>(outA);
-            if (mode == 2) *reinterpret_cast<uint4 *>(a + s_base2[it] + off) = *reinterpret_cast<const uint4 *>(outB);
+            *reinterpret_cast<uint4 *>(a + s_base[k][it] + off) = *reinterpret_cast<const uint4 *>(outA);
+            if (mode == 2) *reinterpret_cast<uint4 *>(a + s_base2[k][it] + off) = *reinterpret_cast<const uint4 *>(outB);
         }
-        __syncthreads();
+        __syncthreads();  // slot k is free for the batch after next
     }
+    cp_async_wait<0>();
 }
 
 }  // namespace
@@ -149,7 +172,7 @@ void launch_permute(int dtype, void *state, int n, const std::vector<std::pair<i
         if (((used >> p) & 1) || ((used >> q) & 1)) fail(SV_ERR_ARG, "permute: pairs not disjoint");
         used |= (1ull << p) | (1ull << q);
     }
-    if (n <= 10) {
+    if ((size_t(1) << n) * (dtype == SV_C64 ? 8 : 16) <= (size_t)kUnitsPerCta * 16) {
         // the whole state is one tile
         A.L0 = n;
         A.vbits = n;
@@ -196,11 +219,26 @@ void launch_permute(int dtype, void *state, int n, const std::vector<std::pair<i
     A.nitems = int64_t(1) << (n - A.vbits);
     if (A.ib > A.nitems) A.ib = (int)A.nitems;
     const int64_t nbatch = (A.nitems + A.ib - 1) / A.ib;
-    const int grid = (int)std::min<int64_t>(nbatch, (int64_t)num_sms() * 6);
+    // two slots x two sides of kUnitsPerCta 16-byte units: 32 KiB, six CTAs per SM
+    const size_t smem = (size_t)4 * kUnitsPerCta * 16;
+    int per_sm = 0;
+    if (dtype == SV_C64) {
+        check_cuda(cudaFuncSetAttribute(k_permute<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(permute)");
+        check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_permute<float2>, kThreads, smem),
+                   "occupancy(permute)");
+    } else {
+        check_cuda(cudaFuncSetAttribute(k_permute<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(permute)");
+        check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_permute<double2>, kThreads, smem),
+                   "occupancy(permute)");
+    }
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<int64_t>(nbatch, (int64_t)num_sms() * per_sm * 32);
     if (dtype == SV_C64)
-        k_permute<float2><<<grid, kThreads, 0, st>>>((float2 *)state, A);
+        k_permute<float2><<<grid, kThreads, smem, st>>>((float2 *)state, A);
     else
-        k_permute<double2><<<grid, kThreads, 0, st>>>((double2 *)state, A);
+        k_permute<double2><<<grid, kThreads, smem, st>>>((double2 *)state, A);
     check_cuda(cudaGetLastError(), "permute kernel launch");
 }
 
