@@ -18,7 +18,7 @@ struct sv_batch {
     int nops = 0;
     int64_t total = 0;
     double bytes = 0;
-    int use_tc = 0;
+    int use_tc = 0;  // 1: tensor-core sections, two pools a CTA; 2: three pools (chunks of <= 12 bits)
     uint64_t wait_ns = sv::kDefaultWaitNs;          // bound of the kernel's waits
     cudaGraph_t graph[2] = {nullptr, nullptr};     // per SV_BATCH_FROM_ZERO value
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -103,6 +103,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
     std::vector<unsigned char> progs;
     // tensor-core sections (complex64 chunks of >= 11 bits): groups fused in FP64 on the GPU
     const bool want_tc = base.use_tc != 0;
+    const bool tc3 = want_tc && std::min(std::max(base.chunk_bits, 6), kBatchMaxChunkBits) <= kBatchTc3ChunkBits;
     std::vector<ComposeSeg> compose;
     std::vector<DevGate<double>> compose_gates;
     // per-state planning and program building, spread over host threads (each state into its own
@@ -203,7 +204,11 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
                     const size_t g_next = gates_in + segs[p1].gates.size();
                     const size_t body = tc ? (p1 + 1 - p0) * (size_t)kBatchTcGroupBytes : g_next * sizeof(DevGate<float>);
                     const size_t bytes = 16 + ((p1 + 1 - p0) * sizeof(DevSeg) + 15) / 16 * 16 + body;
-                    const size_t limit = want_tc ? (size_t)kBatchMaxProgBytesTc : (size_t)kBatchMaxProgBytes;
+                    // SIMT pieces fit every kernel's buffer (a batch whose sections all stay on
+                    // SIMT groups runs the SIMT kernel, whose buffer is the smallest)
+                    const size_t limit = !tc ? (size_t)kBatchMaxProgBytes
+                                         : tc3 ? (size_t)kBatchMaxProgBytesTc3
+                                               : (size_t)kBatchMaxProgBytesTc;
                     if (bytes > limit && p1 > p0) break;
                     if (bytes > limit) fail(SV_ERR_UNSUPPORTED, "register group too large");
                     gates_in = g_next;
@@ -378,7 +383,7 @@ sv_status sv_batch_create(int32_t count, const sv_handle *states, const sv_gate 
             throw;
         }
         cudaFree(tmp);
-        b->use_tc = 1;
+        b->use_tc = tc3 ? 2 : 1;
     }
     *out = b.release();
     SV_API_END

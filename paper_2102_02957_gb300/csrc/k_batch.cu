@@ -56,7 +56,6 @@ __device__ __forceinline__ int find_op(const BatchOp *ops, int nops, int64_t ite
     return lo;
 }
 
-constexpr int kMaxRuns = 1 << (kBatchMaxChunkBits - 4);  // chunk runs above a low run of >= 4 bits
 
 template <int NT>
 __device__ __forceinline__ void copy_prog(unsigned char *dst, const unsigned char *src, int bytes, int ctid) {
@@ -66,27 +65,31 @@ __device__ __forceinline__ void copy_prog(unsigned char *dst, const unsigned cha
 
 // A CTA holds POOLS independent workers ("pools") of NT threads; each drains the queue on its
 // own with its own chunk and program buffers and its own named barrier.  SIMT batches: one pool
-// of 256 threads, two CTAs per SM.  Tensor-core batches: two pools of 128 threads (one 128-row
-// tile each) in one CTA per SM, sharing its 512 tensor-memory columns (192 per pool).
+// of 256 threads, two CTAs per SM.  Tensor-core batches: pools of 128 threads (one 128-row tile
+// each) in one CTA per SM sharing its 512 tensor-memory columns: two pools of two tile buffers
+// for chunks of up to 13 bits, or three of one buffer for chunks of up to 12 bits (more
+// independent tile chains in flight; the smaller chunk buffers make room for the third).
 template <int NT, int POOLS>
 __device__ __forceinline__ void pool_sync(int p) {
     if constexpr (POOLS == 1) __syncthreads();
     else ptx::named_bar_sync(1 + p, NT);
 }
 
-template <int NT, int POOLS>
-__global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const BatchOp *__restrict__ ops, int nops,
+template <int NT, int POOLS, int NB>
+__global__ void __launch_bounds__(NT * POOLS, POOLS >= 2 ? 1 : 2) k_batch(const BatchOp *__restrict__ ops, int nops,
                                                       const unsigned char *__restrict__ progs, float2 *const *amps,
                                                       int *ops_done, int *chunks_done, unsigned long long *next,
                                                       int64_t total, int from_zero, int prog_cap, int *err,
                                                       uint64_t wait_ns, int stall_state) {
-    constexpr bool TC = POOLS == 2;  // the tensor-core configuration
+    constexpr bool TC = POOLS >= 2;  // the tensor-core configurations
+    constexpr int kCapBits = POOLS == 3 ? kBatchTc3ChunkBits : kBatchMaxChunkBits;  // chunk buffer
+    constexpr int kMaxRuns = 1 << (kCapBits - 4);  // chunk runs above a low run of >= 4 bits
     extern __shared__ __align__(16) unsigned char smem[];
     const int p = threadIdx.x / NT, ctid = threadIdx.x % NT;
-    const size_t pool_bytes = (size_t(1) << kBatchMaxChunkBits) * sizeof(float2) + (size_t)prog_cap;
+    const size_t pool_bytes = (size_t(1) << kCapBits) * sizeof(float2) + (size_t)prog_cap;
     float2 *chunk = reinterpret_cast<float2 *>(smem + (size_t)p * pool_bytes);
     const uint32_t chunk_s = ptx::smem_addr(chunk);
-    unsigned char *sprog = reinterpret_cast<unsigned char *>(chunk) + (size_t(1) << kBatchMaxChunkBits) * sizeof(float2);
+    unsigned char *sprog = reinterpret_cast<unsigned char *>(chunk) + (size_t(1) << kCapBits) * sizeof(float2);
     __shared__ int64_t s_item[POOLS], s_next[POOLS];
     __shared__ int s_op[POOLS], s_cached[POOLS], s_abort[POOLS];
     __shared__ BatchOp s_bop[POOLS];
@@ -115,7 +118,8 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
     }
     __syncthreads();
     if constexpr (TC) ptx::tc_fence_after();
-    const uint32_t tmem_pool = TC ? s_tmem + (uint32_t)(p * 2 * TcGeom<4>::COLS) : 0u;
+    static_assert(!TC || POOLS * NB * TcGeom<4>::COLS <= 512, "tile buffers exceed tensor memory");
+    const uint32_t tmem_pool = TC ? s_tmem + (uint32_t)(p * NB * TcGeom<4>::COLS) : 0u;
     uint32_t mma_phase[2] = {0, 0};
     BatchOp &op = s_bop[p];
     while (true) {
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
                     // fused group on the tensor cores, unbiased per row (the batch has no
                     // per-circuit norm restoration); the return value is uniform over the pool
                     if constexpr (TC) {
-                        if (!run_segment_tc<4, NT, true>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)),
+                        if (!run_segment_tc<4, NT, true, NB>(chunk_s, seg_s + (uint32_t)(si * sizeof(DevSeg)),
                                                       body_s + (uint32_t)(si * kBatchTcGroupBytes), ctid, c_swz64, ce,
                                                       tmem_pool, 1 + p, s_mma[p], mma_phase, &s_tc_abort[p],
                                                       &s_wait_ns)) {
@@ -243,10 +247,11 @@ __global__ void __launch_bounds__(NT * POOLS, POOLS == 2 ? 1 : 2) k_batch(const 
 void launch_batch(const void *dev_ops, int nops, const void *dev_progs, void *const *dev_amps, int *dev_ops_done,
                   int *dev_chunks_done, unsigned long long *dev_next, int64_t total, int from_zero, int use_tc,
                   int *dev_err, cudaStream_t st, uint64_t wait_ns, int stall_state) {
-    const int prog_cap = use_tc ? kBatchMaxProgBytesTc : kBatchMaxProgBytes;
-    const int pools = use_tc ? 2 : 1, nt = use_tc ? 128 : 256;
-    const size_t smem = (size_t)pools * ((size_t(1) << kBatchMaxChunkBits) * sizeof(float2) + (size_t)prog_cap);
-    auto kern = use_tc ? k_batch<128, 2> : k_batch<256, 1>;
+    const int prog_cap = use_tc == 2 ? kBatchMaxProgBytesTc3 : use_tc ? kBatchMaxProgBytesTc : kBatchMaxProgBytes;
+    const int pools = use_tc == 2 ? 3 : use_tc ? 2 : 1, nt = use_tc ? 128 : 256;
+    const int cap_bits = use_tc == 2 ? kBatchTc3ChunkBits : kBatchMaxChunkBits;
+    const size_t smem = (size_t)pools * ((size_t(1) << cap_bits) * sizeof(float2) + (size_t)prog_cap);
+    auto kern = use_tc == 2 ? k_batch<128, 3, 1> : use_tc ? k_batch<128, 2, 2> : k_batch<256, 1, 1>;
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "cudaFuncSetAttribute(batch)");
     int per_sm = 0;

@@ -203,6 +203,10 @@ struct BatchOp {
 constexpr int kBatchMaxChunkBits = 13;
 constexpr int kBatchMaxProgBytes = 24 * 1024;    // program piece of a SIMT batch
 constexpr int kBatchMaxProgBytesTc = 32 * 1024;  // ... of a batch with tensor-core sections (per pool)
+// Tensor-core batches whose chunks have at most kBatchTc3ChunkBits bits run three pools per CTA
+// (one tile buffer each) with program pieces of at most kBatchMaxProgBytesTc3 bytes.
+constexpr int kBatchTc3ChunkBits = 12;
+constexpr int kBatchMaxProgBytesTc3 = 38 * 1024;
 constexpr int kBatchTcGroupBytes = TC_B_BYTES + 16;  // B operand + unitarity flag per group
 // wait_ns bounds every device wait; stall_state >= 0 (a failure-path test) keeps that state's first
 // section from releasing the later ones.
