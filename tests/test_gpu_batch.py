@@ -203,3 +203,17 @@ def test_batch_tensor_core_multi_section_from_zero(sv):
     finally:
         for s in states:
             s.close()
+
+
+@pytest.mark.parametrize("chunk_bits", [12, 13])
+def test_batch_tensor_cores_requested_long_simt_programs(sv, chunk_bits):
+    """Tensor cores requested, but every state fits a chunk of fewer than 11 bits, so every
+    section stays on SIMT groups and the SIMT kernel runs: program pieces of long circuits
+    (300+ gates in one residency) must fit its buffer."""
+    ns = [9, 10, 8]
+    descs = [cg.random_layers(n, 40, 50 + n) for n in ns]
+    out, (items, sections, _) = _run_batch(sv, ns, descs, False, chunk_bits=chunk_bits, use_tc=1)
+    assert sections == len(ns)
+    for n, d, got in zip(ns, descs, out):
+        assert len(d) > 300
+        assert_close(got, sim.simulate(n, d), "c64")
