@@ -153,6 +153,11 @@ typedef struct sv_plan_info {
     int32_t final_map[64];       /* physical bit of logical qubit q after the plan   */
 } sv_plan_info;
 sv_status sv_plan_get_info(sv_plan_h plan, sv_plan_info *info);
+/* Register-group width (bits) of every blocking section's tensor-core groups, in plan order: the
+ * plan's seg_bits, or the section's own width where a steered plan chose one (4 or 5 bits on a
+ * chunk of at least 2^(width+7) amplitudes).  out (may be NULL) receives at most cap entries;
+ * count receives the number of sections. */
+sv_status sv_plan_get_widths(sv_plan_h plan, int32_t *out, int64_t cap, int64_t *count);
 
 /* Integer serialisation of the schedule (used to compare schedules bit for bit):
  * [n, c, reserve, restore, n_ops, ops..., final_map[n]] with ops

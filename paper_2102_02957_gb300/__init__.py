@@ -82,6 +82,14 @@ class Plan:
         check(lib().sv_plan_get_info(self._h, ctypes.byref(inf)))
         return inf
 
+    def widths(self):
+        """Register-group width of every blocking section (sv_plan_get_widths)."""
+        cnt = ctypes.c_int64()
+        check(lib().sv_plan_get_widths(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros(cnt.value, dtype=np.int32)
+        check(lib().sv_plan_get_widths(self._h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return out
+
     def serialize(self):
         ln = ctypes.c_int64()
         check(lib().sv_plan_serialize(self._h, None, 0, ctypes.byref(ln)))

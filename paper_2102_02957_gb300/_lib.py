@@ -77,6 +77,7 @@ _SIGS = {
     "sv_plan_blocking": (ctypes.c_int, [ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(sv_options), ctypes.POINTER(_VP)]),
     "sv_plan_free": (ctypes.c_int, [_VP]),
     "sv_plan_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(sv_plan_info)]),
+    "sv_plan_get_widths": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sv_plan_serialize": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "sv_apply_circuit": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     "sv_apply_plan_ops": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_int32]),

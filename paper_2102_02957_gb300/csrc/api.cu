@@ -78,6 +78,7 @@ static void validate_gates(int n, const sv_gate *gates, int64_t n_gates) {
 struct BlockProg {
     size_t off;
     int nseg, ngate;
+    int r = 0;         // tensor-core register-group width of the sweep
     GatherLayout lay;  // gathered sections only
     int op_index = -1;
     bool gathered = false;
@@ -86,25 +87,28 @@ struct BlockProg {
 // Tensor-core programs: every register group (r bits) of a section becomes one fused unitary.  A
 // section whose B operands (tc_b_bytes(r) per group: 2, 8 or 32 KiB) would not fit next to the
 // chunk ring in shared memory is split into consecutive sweeps of at most max_tc_segs(r) groups.
-// Appended after the section programs: the composer's work list and the FP64 gate records it
-// reads.
+// A section's width is its own where the plan chose one (steered plans), else the plan's.
+// Appended after the section programs: the composer's work lists, one per width (3, 4, 5 bits),
+// and the FP64 gate records they read.
 static int max_tc_segs(int r) { return r == 3 ? 24 : r == 4 ? 11 : 3; }
 
-static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r, std::vector<unsigned char> &host,
-                              std::vector<BlockProg> &progs, size_t &cs_off, int &ncs, size_t &g_off,
+static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r_plan, std::vector<unsigned char> &host,
+                              std::vector<BlockProg> &progs, size_t (&cs_off)[3], int (&ncs)[3], size_t &g_off,
                               size_t &flag_off) {
-    const int kMaxTcSegs = max_tc_segs(r);
-    const int b_bytes = tc_b_bytes(r);
     host.clear();
     progs.clear();
     auto align = [&](size_t a) {
         while (host.size() % a) host.push_back(0);
     };
-    std::vector<ComposeSeg> cs;
+    std::vector<ComposeSeg> cs[3];  // per width 3, 4, 5
     std::vector<DevGate<double>> dg;
     for (size_t oi = 0; oi < plan->ops.size(); ++oi) {
         const PlanOp &op0 = plan->ops[oi];
         if (op0.kind != 2 && op0.kind != 4) continue;
+        const int r = op0.seg_bits ? op0.seg_bits : r_plan;
+        if (r < 3 || r > 5) fail(SV_ERR_PLAN, "tensor-core register groups have 3, 4 or 5 bits");
+        const int kMaxTcSegs = max_tc_segs(r);
+        const int b_bytes = tc_b_bytes(r);
         int width = std::min(plan->c, plan->n);
         GatherLayout lay{};
         PlanOp local = op0;
@@ -117,6 +121,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r, 
         }
         for (const BlockGate &g : local.gates)
             if (g.ext[0] >= 0 || g.ext[1] >= 0) fail(SV_ERR_PLAN, "tensor-core sections take no gates outside the chunk");
+        if (width - plan->reserve < r + 7) fail(SV_ERR_PLAN, "a section's chunk is too small for its register-group width");
         const std::vector<HostSeg> segs = segment_block(local.gates, width, r, 8);
         for (size_t p0 = 0; p0 < segs.size(); p0 += kMaxTcSegs) {
             const size_t p1 = std::min(segs.size(), p0 + (size_t)kMaxTcSegs);
@@ -124,6 +129,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r, 
             bp.lay = lay;
             bp.gathered = op0.kind == 4;
             bp.op_index = (int)oi;
+            bp.r = r;
             align(256);
             bp.off = host.size();
             bp.nseg = (int)(p1 - p0);
@@ -156,16 +162,19 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r, 
                 }
                 c.g1 = (int32_t)dg.size();
                 c.b_off = (uint32_t)(b_base + (k - p0) * b_bytes);
-                cs.push_back(c);
+                cs[r - 3].push_back(c);
             }
             progs.push_back(bp);
         }
     }
-    align(256);
-    cs_off = host.size();
-    ncs = (int)cs.size();
-    const unsigned char *p = reinterpret_cast<const unsigned char *>(cs.data());
-    host.insert(host.end(), p, p + cs.size() * sizeof(ComposeSeg));
+    const unsigned char *p = nullptr;
+    for (int w = 0; w < 3; ++w) {
+        align(256);
+        cs_off[w] = host.size();
+        ncs[w] = (int)cs[w].size();
+        p = reinterpret_cast<const unsigned char *>(cs[w].data());
+        host.insert(host.end(), p, p + cs[w].size() * sizeof(ComposeSeg));
+    }
     align(256);
     g_off = host.size();
     p = reinterpret_cast<const unsigned char *>(dg.data());
@@ -447,6 +456,19 @@ sv_status sv_plan_get_info(sv_plan_h p, sv_plan_info *info) {
     SV_API_END
 }
 
+sv_status sv_plan_get_widths(sv_plan_h p, int32_t *out, int64_t cap, int64_t *count) {
+    SV_API_BEGIN
+    if (!p || !count || cap < 0) fail(SV_ERR_ARG, "null argument");
+    int64_t k = 0;
+    for (const PlanOp &op : p->ops) {
+        if (op.kind != 2 && op.kind != 4) continue;
+        if (out && k < cap) out[k] = op.seg_bits ? op.seg_bits : p->seg_bits;
+        ++k;
+    }
+    *count = k;
+    SV_API_END
+}
+
 sv_status sv_plan_serialize(sv_plan_h p, int64_t *buf, int64_t cap, int64_t *len) {
     SV_API_BEGIN
     if (!p || !len) fail(SV_ERR_ARG, "null argument");
@@ -540,8 +562,8 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         // tensor cores: complex64 with chunks of at least 128 rows of the plan's r-bit groups
         const int tc_bits = plan->seg_bits;
         const bool tc = plan->use_tc && h->dtype == SV_C64 && std::min(plan->c, plan->n) - plan->reserve >= tc_bits + 7;
-        size_t cs_off = 0, g_off = 0, flag_off = 0;
-        int ncs = 0;
+        size_t cs_off[3] = {0, 0, 0}, g_off = 0, flag_off = 0;
+        int ncs[3] = {0, 0, 0};
         if (tc) build_programs_tc(plan, gates, tc_bits, host, progs, cs_off, ncs, g_off, flag_off);
         else if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
         else build_programs<double>(plan, gates, seg_bits, host, progs);
@@ -557,8 +579,11 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         const bool renorm = tc && !plan->tc_no_renorm;
         if (tc) {  // fuse every register group into its B operand, in FP64 on the GPU
             ensure_scratch(h, (size_t)(2 * nb_norm + 2) * sizeof(double));
-            launch_compose(base + cs_off, ncs, base + g_off, h->prog, unitary_flag, tc_bits, h->stream);
-            ++st.kernel_launches;
+            for (int w = 0; w < 3; ++w)
+                if (ncs[w]) {
+                    launch_compose(base + cs_off[w], ncs[w], base + g_off, h->prog, unitary_flag, w + 3, h->stream);
+                    ++st.kernel_launches;
+                }
         }
         if (renorm) {
             launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb_norm, h->stream);
@@ -574,7 +599,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
                     mark_begin(h, 1, (int)oi);
                     if (tc)
                         launch_block_tc(h->amp, h->n, plan->c, bp.gathered ? &bp.lay : nullptr, base + bp.off, bp.nseg,
-                                        h->dev_err, tc_bits, h->stream, wait_ns);
+                                        h->dev_err, bp.r, h->stream, wait_ns);
                     else if (!bp.gathered)
                         launch_block(h->dtype, h->amp, h->n, plan->c, base + bp.off, bp.nseg, bp.ngate, h->dev_err,
                                      seg_bits, h->stream, wait_ns);

@@ -122,15 +122,41 @@ struct RandomChooser : SectionChooser {
     }
 };
 
-// Most gates per predicted microsecond; the paper's rule (candidate 0) wins ties.
+// Most gates per predicted microsecond; the paper's rule (candidate 0) wins ties.  The planner
+// asks once or twice per section, so the network is evaluated on the host from a copy of its
+// parameters taken when the chooser is made (16 -> 64 -> 64 -> 1, the layout of k_mlp.cu), not
+// by a kernel launch and a synchronisation per question.
 struct ModelChooser : SectionChooser {
     sv_costmodel *m;
-    explicit ModelChooser(sv_costmodel *mm) : m(mm) {}
+    std::vector<float> P;
+    explicit ModelChooser(sv_costmodel *mm) : m(mm), P((size_t)mlp_param_count()) {
+        check_cuda(cudaMemcpyAsync(P.data(), m->params, P.size() * sizeof(float), cudaMemcpyDeviceToHost, m->stream),
+                   "D2H(cost model)");
+        check_cuda(cudaStreamSynchronize(m->stream), "cudaStreamSynchronize");
+    }
+    double predict_us_host(const float *x) const {
+        constexpr int NIN = NF, NH = 64;
+        const float *W1 = P.data(), *b1 = W1 + NH * NIN, *W2 = b1 + NH, *b2 = W2 + NH * NH, *w3 = b2 + NH;
+        const float b3 = w3[NH];
+        float h1[NH], h2[NH];
+        for (int u = 0; u < NH; ++u) {
+            float a = b1[u];
+            for (int f = 0; f < NIN; ++f) a += W1[u * NIN + f] * x[f];
+            h1[u] = a > 0.f ? a : 0.f;
+        }
+        float y = b3;
+        for (int u = 0; u < NH; ++u) {
+            float a = b2[u];
+            for (int f = 0; f < NH; ++f) a += W2[u * NH + f] * h1[f];
+            h2[u] = a > 0.f ? a : 0.f;
+            y += w3[u] * h2[u];
+        }
+        return std::exp((double)y * m->t_std + m->t_mean);
+    }
     int choose(const std::vector<SectionCandidate> &c) override {
         if (c.size() <= 1) return 0;
-        std::vector<float> x(c.size() * NF);
-        for (size_t k = 0; k < c.size(); ++k) std::memcpy(&x[k * NF], c[k].f, sizeof(c[k].f));
-        const std::vector<float> us = predict_us(m, x.data(), (int64_t)c.size());
+        std::vector<double> us(c.size());
+        for (size_t k = 0; k < c.size(); ++k) us[k] = predict_us_host(c[k].f);
         int best = 0;
         double best_rate = (double)c[0].absorbed / std::max(1e-3, (double)us[0]);
         for (size_t k = 1; k < c.size(); ++k) {

@@ -191,16 +191,17 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     while (!remaining.empty()) {
         // choose QB_CHUNK
         uint64_t chosen = (pinned && o.lookahead && !chooser) ? greedy_select(target) : rule_select(target);
+        int chosen_r = 0;  // this section's register-group width (0: the plan's)
         if (chooser && pinned) {
             cands.clear();
-            auto add_candidate = [&](uint64_t ch) {
-                for (const SectionCandidate &c0 : cands)
-                    if (c0.chosen == ch) return;
+            auto make_candidate = [&](uint64_t ch, int r) {
                 SectionCandidate cd;
                 cd.chosen = ch;
                 cd.ce = popc(ch);
+                cd.seg_bits = r;
                 PlanOp tmp;
                 tmp.kind = 4;
+                tmp.seg_bits = r;
                 uint64_t blocked = 0, out_blocked = 0;
                 for (const PG &g : remaining) {
                     if (takes(g, ch, blocked, out_blocked)) {
@@ -219,7 +220,12 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
                     if ((ch >> v) & 1) tmp.mask |= 1ull << m[v];
                 cd.absorbed = (int)tmp.gates.size();
                 section_features(*plan, tmp, gates, dtype, cd.f);
-                cands.push_back(cd);
+                return cd;
+            };
+            auto add_candidate = [&](uint64_t ch) {
+                for (const SectionCandidate &c0 : cands)
+                    if (c0.chosen == ch) return;
+                cands.push_back(make_candidate(ch, 0));
             };
             add_candidate(chosen);
             // smaller chunks (still room for a 2-qubit gate; >= 11 bits for the tensor-core path)
@@ -228,6 +234,20 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
                 if (target - d >= min_t && target - d >= remaining.front().nq + pinned) add_candidate(rule_select(target - d));
             add_candidate(greedy_select(target));
             chosen = cands[(size_t)std::max(0, std::min((int)cands.size() - 1, chooser->choose(cands)))].chosen;
+            // the register-group width of the section's tensor-core groups: the plan's, or 4 or 5
+            // bits where the chunk has room (at least 2^(r+7) amplitudes), as the chooser picks
+            // (every width takes the same gates, so the model's choice is the lowest predicted time)
+            if (o.use_tc && dtype == SV_C64) {
+                std::vector<SectionCandidate> widths;
+                const int ce = popc(chosen);
+                for (int r : {plan->seg_bits, 4, 5}) {
+                    bool dup = false;
+                    for (const SectionCandidate &w0 : widths) dup = dup || w0.seg_bits == r;
+                    if (!dup && ce >= r + 7) widths.push_back(make_candidate(chosen, r));
+                }
+                if (widths.size() > 1)
+                    chosen_r = widths[(size_t)std::max(0, std::min((int)widths.size() - 1, chooser->choose(widths)))].seg_bits;
+            }
         }
 
         // chunk_swap round (none for gathered chunks: the section fetches its bits in place)
@@ -252,6 +272,7 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         // scan REMAINING with QB_BLOCKED
         PlanOp block;
         block.kind = pinned ? 4 : 2;
+        block.seg_bits = chosen_r == plan->seg_bits ? 0 : chosen_r;
         if (pinned)
             for (int v = 0; v < n; ++v)
                 if ((chosen >> v) & 1) block.mask |= 1ull << m[v];
@@ -454,7 +475,7 @@ bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t>
 
 }  // namespace
 
-std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes) {
+std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes, bool search) {
     std::vector<HostSeg> segs;
     std::vector<int32_t> pending(gates.size());
     std::iota(pending.begin(), pending.end(), 0);
@@ -468,7 +489,7 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
     const int rr = std::min(r, width);
     // the group sets: the search's, else the greedy choice
     std::vector<uint64_t> sets;
-    if (!beam_groups(mask, rr, sets)) sets.clear();
+    if (!search || !beam_groups(mask, rr, sets)) sets.clear();
     if (sets.empty() && !pending.empty()) {
         // a gate with no chunk bit (a diagonal wholly outside the chunk) fits every group
         bool any_outside = false;
@@ -760,11 +781,12 @@ int plan_segment_count(const sv_plan &plan) {
     int nseg = 0;
     const int n = plan.n, c = plan.c;
     for (const PlanOp &op : plan.ops) {
+        const int r = op.seg_bits ? op.seg_bits : plan.seg_bits;
         if (op.kind == 2)
-            nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), plan.seg_bits, 8).size();
+            nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), r, 8).size();
         if (op.kind == 4) {
             const GatherLayout L = gather_layout(op.mask, n, 8);
-            nseg += (int)segment_block(localize_gates(op, n, c, &L), L.ce, plan.seg_bits, 8).size();
+            nseg += (int)segment_block(localize_gates(op, n, c, &L), L.ce, r, 8).size();
         }
     }
     return nseg;
@@ -806,8 +828,9 @@ void section_features(const sv_plan &plan, const PlanOp &op, const sv_gate *gate
     } else {
         loc = localize_gates(op, n, plan.c, nullptr);
     }
-    const bool tc = plan.use_tc && dtype == SV_C64 && ce >= plan.seg_bits + 7;
-    const int r = tc ? plan.seg_bits : (dtype == SV_C64 && plan.seg_bits == 5 ? 5 : 4);
+    const int tc_r = op.seg_bits ? op.seg_bits : plan.seg_bits;
+    const bool tc = plan.use_tc && dtype == SV_C64 && ce >= tc_r + 7;
+    const int r = tc ? tc_r : (dtype == SV_C64 && plan.seg_bits == 5 ? 5 : 4);
     const int nseg = loc.empty() ? 0 : (int)segment_block(loc, ce, r, 8).size();
     int q_total = 0, two = 0, cheap = 0;
     float hist[6] = {0, 0, 0, 0, 0, 0};

@@ -40,6 +40,7 @@ struct PlanOp {
     std::vector<std::pair<int32_t, int32_t>> pairs;
     std::vector<BlockGate> gates;
     uint64_t mask = 0;  // chunk bits of a gathered block
+    int32_t seg_bits = 0;  // tensor-core register-group width of this block (0: the plan's)
 };
 
 struct GateKey {
@@ -69,6 +70,7 @@ struct SectionCandidate {
     uint64_t chosen = 0;  // qubits of the chunk
     int absorbed = 0;     // gates the section takes
     int ce = 0;           // chunk bits
+    int seg_bits = 0;     // register-group width the features assume (0: the plan's)
     float f[kNumFeatures] = {0};
 };
 struct SectionChooser {
@@ -141,7 +143,9 @@ struct HostSeg {
 
 // Split a section's gates (physical bits < width) into register groups of at most r bits,
 // and choose each group's lane layout for elements of elem_bytes bytes.
-std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes);
+// search = false: the greedy groups only (the cost model's cheap feature).
+std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int width, int r, int elem_bytes,
+                                   bool search = true);
 int plan_segment_count(const sv_plan &plan);
 
 template <typename T>

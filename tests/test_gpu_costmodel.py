@@ -223,3 +223,32 @@ def test_steered_planner_gain_on_held_out_circuits(sv, trained):
     total_steer = sum(r[6] for r in rows)
     print(f"total gain vs rule {total_rule / total_steer:.3f}x, vs look-ahead {total_look / total_steer:.3f}x")
     assert total_steer <= 0.98 * total_rule
+
+
+def test_steered_section_widths_give_oracle_state(sv):
+    """A steered plan picks each section's register-group width (4 or 5 bits) by the network's
+    predicted time; networks fitted briefly to random timings (several seeds) choose differently
+    from section to section, and a plan mixing both widths must still give the oracle's state."""
+    n = 20
+    desc = cg.quantum_volume(n, 10, 81)
+    g = sv.make_gates(desc)
+    mixed = None
+    for seed in range(12):
+        rng = np.random.Generator(np.random.PCG64(100 + seed))
+        cm = sv.CostModel(seed)
+        cm.add_samples(rng.uniform(0.0, 1.0, (64, 16)).astype(np.float32),
+                       np.exp(rng.normal(5.0, 1.0, 64)).astype(np.float32))
+        cm.train(epochs=2, batch=32, lr=1e-3, seed=seed)
+        plan = sv.Plan(n, g, model=cm, chunk_bits=13, gather_pinned=4, use_tc=1)
+        w = set(int(x) for x in plan.widths())
+        assert w <= {4, 5}
+        if w == {4, 5}:
+            mixed = plan
+            break
+    assert mixed is not None, "no seed gave a plan with both widths"
+    with sv.StateVector(n, "c64") as st:
+        st.init_basis(0)
+        st.apply(g, mixed)
+        st.synchronize()
+        assert_close(st.get_state(), sim.simulate(n, desc), "c64")
+    assert mixed.info().n_segments > 0

@@ -241,3 +241,17 @@ def test_lookahead_plans_valid_and_equivalent(sv, n, c, pinned):
     g = sv.make_gates(qv)
     assert (sv.Plan(n, g, chunk_bits=c, gather_pinned=pinned, lookahead=1).info().n_blocks
             <= sv.Plan(n, g, chunk_bits=c, gather_pinned=pinned).info().n_blocks)
+
+
+@pytest.mark.parametrize("seg_bits", [3, 4, 5])
+def test_plan_widths_default_to_the_plan(sv, seg_bits):
+    """Plans made without a cost model give every section the plan's register-group width; the
+    group count of the plan info is the sum of the per-section beam-search groups, which never
+    exceeds one group per gate."""
+    n = 22
+    g = sv.make_gates(cg.quantum_volume(n, 10, 5))
+    plan = sv.Plan(n, g, chunk_bits=12, gather_pinned=5, use_tc=1, seg_bits=seg_bits, lookahead=1)
+    w = plan.widths()
+    inf = plan.info()
+    assert len(w) == inf.n_blocks and set(int(x) for x in w) == {seg_bits}
+    assert inf.n_blocks <= inf.n_segments <= inf.n_gates_emitted
