@@ -23,6 +23,34 @@
 namespace sv {
 namespace {
 
+// Slab copies by a kernel, for host memory the GPU can address directly (pinned and mapped):
+// sub-state amplitude j = (slab e << m) | w lives in host amplitude base | dep(e) | w, dep(e)
+// depositing e's bit t at state bit high[t].  One 16-byte unit per thread and step; IN copies
+// host -> sub-state, else sub-state -> host.  Used where the slabs are small, so that a pass is a
+// few launches instead of thousands of tiny copies.
+struct SlabArgs {
+    int m, nh, lg_apu;  // slab bits, |H|, log2 amplitudes per 16-byte unit
+    int8_t high[64];
+    int64_t base;       // state index of the sub-state's first amplitude
+    int64_t units;      // 16-byte units of the sub-state
+};
+
+template <bool IN>
+__global__ void __launch_bounds__(256) k_slab_copy(uint4 *__restrict__ dev, uint4 *__restrict__ host, SlabArgs a) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < a.units; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = u << a.lg_apu;  // sub-state amplitude of the unit's first element
+        const int64_t e = j >> a.m;
+        int64_t x = a.base | (j & ((int64_t(1) << a.m) - 1));
+        for (int t = 0; t < a.nh; ++t)
+            if ((e >> t) & 1) x |= int64_t(1) << a.high[t];
+        const int64_t hu = x >> a.lg_apu;
+        if (IN) dev[u] = host[hu];
+        else host[hu] = dev[u];
+    }
+}
+
+constexpr size_t kKernelSlabBytes = size_t(1) << 20;  // slabs below 1 MiB go through k_slab_copy
+
 struct PassItem {
     int op;                                          // plan op
     std::vector<std::pair<int32_t, int32_t>> pairs;  // swap pairs of this item (rounds only)
@@ -101,8 +129,9 @@ std::vector<Pass> make_passes(const sv_plan &plan, int M) {
 // Run one pass: for every value of the state bits >= m outside H, gather the sub-state's 2^|H|
 // slabs, run the pass's items on it, write it back.  Sub-states alternate between the two halves
 // of the work buffer and the two streams.
-void run_pass(const Pass &p, const sv_plan &plan, int dtype, unsigned char *host, unsigned char *work, size_t half_bytes,
-              const unsigned char *prog, const SimtPrograms &sp, int *dev_err, cudaStream_t *st, uint64_t wait_ns) {
+void run_pass(const Pass &p, const sv_plan &plan, int dtype, unsigned char *host, unsigned char *host_dev,
+              unsigned char *work, size_t half_bytes, const unsigned char *prog, const SimtPrograms &sp, int *dev_err,
+              cudaStream_t *st, uint64_t wait_ns) {
     const int n = plan.n, m = p.m, nh = (int)p.high.size(), nsub = m + nh;
     const size_t elem = dtype == SV_C64 ? 8 : 16;
     const size_t slab_bytes = (size_t(1) << m) * elem;
@@ -119,6 +148,16 @@ void run_pass(const Pass &p, const sv_plan &plan, int dtype, unsigned char *host
     for (size_t i = 0; i < p.items.size(); ++i)
         for (const auto &pq : p.items[i].pairs) pairs[i].emplace_back(local_bit(pq.first), local_bit(pq.second));
     const int64_t nsubs = int64_t(1) << outer.size();
+    // small slabs (passes that carry many high swap bits) move by kernel when the host memory is
+    // mapped into the device's address space
+    const bool by_kernel = host_dev && slab_bytes < kKernelSlabBytes;
+    SlabArgs sa{};
+    sa.m = m;
+    sa.nh = nh;
+    sa.lg_apu = elem == 8 ? 1 : 0;
+    for (int t = 0; t < nh; ++t) sa.high[t] = (int8_t)p.high[(size_t)t];
+    sa.units = (int64_t)(((size_t(1) << nsub) * elem) / 16);
+    const unsigned grid = (unsigned)std::min<int64_t>((sa.units + 255) / 256, (int64_t)num_sms() * 8);
     for (int64_t o = 0; o < nsubs; ++o) {
         const int k = (int)(o & 1);
         unsigned char *buf = work + (size_t)k * half_bytes;
@@ -131,10 +170,16 @@ void run_pass(const Pass &p, const sv_plan &plan, int dtype, unsigned char *host
                 if ((e >> t) & 1) x |= int64_t(1) << p.high[(size_t)t];
             return host + (size_t)x * elem;
         };
-        for (int e = 0; e < (1 << nh); ++e)
-            check_cuda(cudaMemcpyAsync(buf + (size_t)e * slab_bytes, slab_host(e), slab_bytes, cudaMemcpyHostToDevice,
-                                       st[k]),
-                       "cudaMemcpyAsync(host slab in)");
+        sa.base = base;
+        if (by_kernel) {
+            k_slab_copy<true><<<grid, 256, 0, st[k]>>>(reinterpret_cast<uint4 *>(buf), reinterpret_cast<uint4 *>(host_dev), sa);
+            check_cuda(cudaGetLastError(), "slab gather launch");
+        } else {
+            for (int e = 0; e < (1 << nh); ++e)
+                check_cuda(cudaMemcpyAsync(buf + (size_t)e * slab_bytes, slab_host(e), slab_bytes, cudaMemcpyHostToDevice,
+                                           st[k]),
+                           "cudaMemcpyAsync(host slab in)");
+        }
         for (size_t i = 0; i < p.items.size(); ++i) {
             const int op = p.items[i].op;
             if (plan.ops[(size_t)op].kind == 2) {
@@ -148,10 +193,15 @@ void run_pass(const Pass &p, const sv_plan &plan, int dtype, unsigned char *host
                 launch_permute(dtype, buf, nsub, pairs[i], st[k]);
             }
         }
-        for (int e = 0; e < (1 << nh); ++e)
-            check_cuda(cudaMemcpyAsync(slab_host(e), buf + (size_t)e * slab_bytes, slab_bytes, cudaMemcpyDeviceToHost,
-                                       st[k]),
-                       "cudaMemcpyAsync(host slab out)");
+        if (by_kernel) {
+            k_slab_copy<false><<<grid, 256, 0, st[k]>>>(reinterpret_cast<uint4 *>(buf), reinterpret_cast<uint4 *>(host_dev), sa);
+            check_cuda(cudaGetLastError(), "slab scatter launch");
+        } else {
+            for (int e = 0; e < (1 << nh); ++e)
+                check_cuda(cudaMemcpyAsync(slab_host(e), buf + (size_t)e * slab_bytes, slab_bytes, cudaMemcpyDeviceToHost,
+                                           st[k]),
+                           "cudaMemcpyAsync(host slab out)");
+        }
     }
 }
 
@@ -208,9 +258,19 @@ extern "C" sv_status sv_apply_circuit_host(int32_t n, int32_t dtype, void *host_
         join(caller, st[0]);
         join(caller, st[1]);
         const uint64_t wait_ns = plan->wait_limit_ms > 0 ? (uint64_t)plan->wait_limit_ms * 1000000ull : kDefaultWaitNs;
+        // the device's address of the host state, if the GPU can address it directly (pinned and
+        // mapped host memory); else every slab goes through a copy
+        unsigned char *host_dev = nullptr;
+        {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, host_amps) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                at.devicePointer != nullptr && (reinterpret_cast<uintptr_t>(at.devicePointer) % 16) == 0)
+                host_dev = static_cast<unsigned char *>(at.devicePointer);
+            cudaGetLastError();  // an unregistered pointer leaves an error state; clear it
+        }
         const std::vector<Pass> passes = make_passes(*plan, M);
         for (const Pass &p : passes) {
-            run_pass(p, *plan, dtype, static_cast<unsigned char *>(host_amps), static_cast<unsigned char *>(dev_work),
+            run_pass(p, *plan, dtype, static_cast<unsigned char *>(host_amps), host_dev, static_cast<unsigned char *>(dev_work),
                      half_bytes, static_cast<const unsigned char *>(progbuf), sp, dev_err, st, wait_ns);
             // the next pass reads what either stream wrote back
             join(st[0], st[1]);
