@@ -255,3 +255,68 @@ def test_plan_widths_default_to_the_plan(sv, seg_bits):
     inf = plan.info()
     assert len(w) == inf.n_blocks and set(int(x) for x in w) == {seg_bits}
     assert inf.n_blocks <= inf.n_segments <= inf.n_gates_emitted
+
+
+def _greedy_groups(masks, r):
+    """Register groups by greedy growth (the first pending gate's bits, then the pending gate,
+    among the first 64 with new bits, that lets the group take the most gates)."""
+    pending = list(range(len(masks)))
+
+    def split(pend, bits):
+        blocked, rest = 0, []
+        for i in pend:
+            if (masks[i] & ~bits) == 0 and (masks[i] & blocked) == 0:
+                continue
+            blocked |= masks[i]
+            rest.append(i)
+        return rest
+
+    groups = 0
+    while pending:
+        s = masks[pending[0]]
+        while bin(s).count("1") < r:
+            best, best_k, tried = 0, -1, 0
+            for i in pending:
+                fresh = masks[i] & ~s
+                if not fresh or bin(s | fresh).count("1") > r:
+                    continue
+                tried += 1
+                if tried > 64:
+                    break
+                k = len(pending) - len(split(pending, s | fresh))
+                if k > best_k:
+                    best_k, best = k, fresh
+            if not best:
+                break
+            s |= best
+        pending = split(pending, s)
+        groups += 1
+    return groups
+
+
+@pytest.mark.parametrize("name,c,pinned", [("qv30", 12, 5), ("qv26", 12, 5), ("rl28", 12, 4)])
+def test_register_group_search_bounds(sv, name, c, pinned):
+    """The library's register groups per plan (beam search) never outnumber greedy growth's
+    (restated here) and never undercut the lower bound ceil(bits in use / r) of any section."""
+    w = cg.WORKLOADS[name]
+    desc = cg.build(name)
+    n = w["n"]
+    lib_plan = sv.Plan(n, sv.make_gates(desc), chunk_bits=c, gather_pinned=pinned, lookahead=1)
+    oracle_plan = planner.plan_blocking(n, desc, c, pinned=pinned, lookahead=True)
+    greedy = bound = 0
+    for bits, gl in oracle_plan.blocks():
+        masks = []
+        for _gi, phys in gl:
+            m = 0
+            for q in phys:
+                if q >= 0:
+                    m |= 1 << q
+            masks.append(m)
+        greedy += _greedy_groups(masks, 4)
+        used = 0
+        for m in masks:
+            used |= m
+        bound += -(-bin(used).count("1") // 4)
+    got = lib_plan.info().n_segments
+    print(f"{name}: beam {got}, greedy {greedy}, lower bound {bound}")
+    assert bound <= got <= greedy
