@@ -390,15 +390,16 @@ struct VecHash {
 };
 
 // Groups by beam search: level by level, every r-subset of the bits the pending gates use is
-// tried on each of the kGroupBeam pending lists kept (subsets in lexicographic order of their bit
+// tried on each of the `width` pending lists kept (subsets in lexicographic order of their bit
 // positions); the children are ranked by the lower bound ceil(|bits used| / r) on the groups they
 // still need, then by pending gates, then by bits used (stable: ties keep the order they were
 // found in), and the first list to empty ends the search.  Returns false once the budget of
 // pending-gate visits is spent.
 constexpr int kGroupBeam = 8;
+constexpr int kGroupBeamMaxGates = 32;  // sections with more gates search with a beam of one
 constexpr int64_t kGroupSearchBudget = 4000000;  // pending-gate visits per section
 
-bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out) {
+bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
     struct Node {
         std::vector<int32_t> pend;
         std::vector<uint64_t> sets;
@@ -467,7 +468,7 @@ bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t>
             if (a.npend != b.npend) return a.npend < b.npend;
             return a.nbits < b.nbits;
         });
-        if (children.size() > (size_t)kGroupBeam) children.resize(kGroupBeam);
+        if (children.size() > (size_t)width) children.resize((size_t)width);
         beam.clear();
         for (Child &c : children) beam.push_back(std::move(c.node));
     }
@@ -489,7 +490,10 @@ std::vector<HostSeg> segment_block(const std::vector<BlockGate> &gates, int widt
     const int rr = std::min(r, width);
     // the group sets: the search's, else the greedy choice
     std::vector<uint64_t> sets;
-    if (!search || !beam_groups(mask, rr, sets)) sets.clear();
+    // long sections (whole small-state circuits in one residency) search with a beam of one: the
+    // full beam's cost grows with the pending lists, and its gain there is a few per cent
+    const int beam = (int)gates.size() > kGroupBeamMaxGates ? 1 : kGroupBeam;
+    if (!search || !beam_groups(mask, rr, sets, beam)) sets.clear();
     if (sets.empty() && !pending.empty()) {
         // a gate with no chunk bit (a diagonal wholly outside the chunk) fits every group
         bool any_outside = false;
