@@ -653,26 +653,28 @@ def run_ours(args):
     if not args.no_e2e:
         h_in = torch.zeros(2 << n, dtype=torch.float32).pin_memory()
         h_in[0] = 1.0
-        h_out = [torch.empty(2 << n, dtype=torch.float32).pin_memory() for _ in range(2)]
-        e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # three states in rotation: step i's upload (state i % 3) can run while step i - 1's
+        # download (another state) is still in flight, the link carrying both directions at once
+        n_rot = 3
+        h_out = [torch.empty(2 << n, dtype=torch.float32).pin_memory() for _ in range(n_rot)]
+        e_streams = [torch.cuda.Stream() for _ in range(n_rot)]
         e_states = [sv.StateVector(n, "c64", stream=s) for s in e_streams]
-
         # the steps' kernels run one step at a time (each step's apply waits for the previous
-        # step's, on the other stream), so that one step's host copies overlap the other's kernels
-        # instead of both states' kernels sharing the GPU while the copies wait
-        computed = [torch.cuda.Event(), torch.cuda.Event()]
+        # step's, on another stream), so that the host copies overlap the kernels instead of
+        # several states' kernels sharing the GPU while the copies wait
+        computed = [torch.cuda.Event() for _ in range(n_rot)]
 
         def e2e_step(i):
-            k = i & 1
+            k, prev = i % n_rot, (i - 1) % n_rot
             g = sv.make_gates(desc)
             p = sv.Plan(n, g, **plan_opts)
             e_states[k].set_state_async(h_in.data_ptr())
-            e_streams[k].wait_event(computed[1 - k])
+            e_streams[k].wait_event(computed[prev])
             e_states[k].apply(g, p)
             computed[k].record(e_streams[k])
             e_states[k].get_state_async(h_out[k].data_ptr())
 
-        for i in range(2):
+        for i in range(n_rot):
             e2e_step(i)
         for s in e_states:
             s.synchronize()
@@ -698,9 +700,9 @@ def run_ours(args):
         dt = bar.max(time.perf_counter() - t0)
         e2e = {"value": world * G * k2 / dt, "unit": "gates/s", "h2d_bytes_per_step": int((2 << n) * 4),
                "d2h_bytes_per_step": int((2 << n) * 4), "ms_per_step": 1000 * dt / k2,
-               "pipeline": "2 states on 2 streams, kernels of one step at a time: one step's host copies overlap the next step's kernels",
+               "pipeline": "3 states on 3 streams in rotation, kernels of one step at a time: uploads and downloads of other steps overlap each step's kernels",
                "host_link": link}
-        out0 = h_out[(k2 - 1) & 1][:2].numpy().copy()
+        out0 = h_out[(k2 - 1) % n_rot][:2].numpy().copy()
         for s in e_states:
             s.close()
         del h_in, h_out
