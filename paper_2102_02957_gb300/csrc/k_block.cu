@@ -8,18 +8,20 @@
 // are read off the chunk's origin index.
 //
 // Kernel organisation (persistent, warp-specialised):
-//  * warp 0, lane 0 is the producer (produce_chunks): it streams the CTA's chunks
+//  * warp 0 is the producer (produce_chunks): it streams the CTA's chunks
 //    j = blockIdx.x + t*gridDim.x into a ring of shared-memory buffers with bulk or tensor
-//    asynchronous copies (TMA engine) completing on "full" mbarriers;
+//    asynchronous copies (TMA engine) completing on "full" mbarriers, each lane issuing its own
+//    boxes of a gathered chunk (lane 0 does the mbarrier bookkeeping);
 //  * G consumer groups of NC threads (two; four for tensor-core sections of chunks up to 12 bits)
 //    take chunks in turn, so one group's shared-memory and barrier phases overlap another's
 //    arithmetic.  For each chunk a group runs the section's
 //    register groups -- SIMT (run_segment: each thread loads the 2^R amplitudes spanned by the
 //    group's R chunk bits into registers, applies every gate of the group there, stores them
 //    back) or tensor cores (run_segment_tc: the group's fused unitary applied to 128-row tiles
-//    with tcgen05 MMAs) -- then hand it to the store thread through a "done" mbarrier;
-//  * warp 1, lane 0 is the store thread (store_chunks): it writes the chunks back in order and
-//    releases each buffer to the producer through an "empty" mbarrier once the copy has read it.
+//    with tcgen05 MMAs) -- then hand it to the store warp through a "done" mbarrier;
+//  * warp 1 is the store warp (store_chunks): it writes the chunks back in order, a box or piece
+//    per lane, and releases each buffer to the producer through an "empty" mbarrier once the
+//    copies have read it.
 //
 // Shared-memory layout of a chunk while it is being worked on: amplitude i sits in slot
 // i ^ F(i), where F XORs a fixed non-zero pattern V[k] into the low slot bits for every set
