@@ -785,7 +785,8 @@ int plan_segment_count(const sv_plan &plan) {
     int nseg = 0;
     const int n = plan.n, c = plan.c;
     for (const PlanOp &op : plan.ops) {
-        const int r = op.seg_bits ? op.seg_bits : plan.seg_bits;
+        // tensor-core plans: the section's width; SIMT register groups have 4 or 5 bits
+        const int r = plan.use_tc ? (op.seg_bits ? op.seg_bits : plan.seg_bits) : (plan.seg_bits == 5 ? 5 : 4);
         if (op.kind == 2)
             nseg += (int)segment_block(localize_gates(op, n, c, nullptr), std::min(c, n), r, 8).size();
         if (op.kind == 4) {
