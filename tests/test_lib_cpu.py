@@ -320,3 +320,19 @@ def test_register_group_search_bounds(sv, name, c, pinned):
     got = lib_plan.info().n_segments
     print(f"{name}: beam {got}, greedy {greedy}, lower bound {bound}")
     assert bound <= got <= greedy
+
+
+def test_plan_widths_arguments(sv):
+    """sv_plan_get_widths: null plan or count and a negative capacity are argument errors; a
+    capacity smaller than the section count fills what fits and still reports the count."""
+    import ctypes
+    lib = sv._lib.lib()
+    g = sv.make_gates(cg.quantum_volume(12, 4, 2))
+    plan = sv.Plan(12, g, chunk_bits=8, gather_pinned=4, use_tc=0)
+    cnt = ctypes.c_int64()
+    assert lib.sv_plan_get_widths(None, None, 0, ctypes.byref(cnt)) == sv._lib.SV_ERR_ARG
+    assert lib.sv_plan_get_widths(plan.handle, None, 0, None) == sv._lib.SV_ERR_ARG
+    assert lib.sv_plan_get_widths(plan.handle, None, -1, ctypes.byref(cnt)) == sv._lib.SV_ERR_ARG
+    out = (ctypes.c_int32 * 1)(-7)
+    assert lib.sv_plan_get_widths(plan.handle, out, 1, ctypes.byref(cnt)) == sv._lib.SV_OK
+    assert cnt.value == plan.info().n_blocks >= 1 and out[0] == 4
