@@ -71,6 +71,15 @@ typedef enum sv_gate_kind {
  * parameters).  out: filled on success.  SV_ERR_ARG for an unknown kind or repeated qubit. */
 sv_status sv_gate_make(int32_t kind, const int32_t *qubits, const double *params, sv_gate *out);
 
+/* Build `count` gate records in one call (the same matrices as sv_gate_make, Sec. II.A).
+ * kinds[count]; qubits[count][2] (the second entry of a 1-qubit kind is ignored);
+ * params[count][param_stride] doubles, read only for kinds that take parameters, so
+ * param_stride must be at least the largest such count among `kinds` (32 covers every kind;
+ * params may be NULL when none takes any).  out[count]: all caller-owned host memory.
+ * On an error no later entry is written; SV_ERR_ARG names the failing index. */
+sv_status sv_gates_make(int64_t count, const int32_t *kinds, const int32_t *qubits, const double *params,
+                        int32_t param_stride, sv_gate *out);
+
 /* Planner / executor options.  Defaults from sv_options_default(). */
 typedef struct sv_options {
     int32_t chunk_bits;     /* c: physical bits 0..c-1 form a chunk (Sec. II.B, IV.A); default 13 */

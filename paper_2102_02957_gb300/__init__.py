@@ -21,23 +21,25 @@ DTYPES = {"c64": SV_C64, "c128": SV_C128, SV_C64: SV_C64, SV_C128: SV_C128}
 
 
 def make_gates(descriptions) -> np.ndarray:
-    """Gate records (sv_gate array) from (kind, qubits, params) descriptions, each built by
-    sv_gate_make in the library."""
-    L = lib()
-    out = np.zeros(len(descriptions), dtype=GATE_DTYPE)
-    q = (ctypes.c_int32 * 2)()
-    for i, (kind, qubits, params) in enumerate(descriptions):
-        for j, v in enumerate(qubits):
-            q[j] = int(v)
+    """Gate records (sv_gate array) from (kind, qubits, params) descriptions, built by the
+    library in one sv_gates_make call."""
+    G = len(descriptions)
+    out = np.zeros(G, dtype=GATE_DTYPE)
+    kinds = np.empty(G, dtype=np.int32)
+    qubits = np.zeros((G, 2), dtype=np.int32)
+    params = np.zeros((G, 32), dtype=np.float64)
+    as_complex = params.view(np.complex128)  # (G, 16): a unitary's row-major entries
+    for i, (kind, qs, ps) in enumerate(descriptions):
+        qubits[i, :len(qs)] = qs
         if kind == "unitary":
-            m = np.ascontiguousarray(params[0], dtype=np.complex128)
-            k = _lib.SV_K_UNITARY1 if m.shape == (2, 2) else _lib.SV_K_UNITARY2
-            p = np.ascontiguousarray(m.reshape(-1).view(np.float64))
+            m = np.asarray(ps[0], dtype=np.complex128)
+            kinds[i] = _lib.SV_K_UNITARY1 if m.shape == (2, 2) else _lib.SV_K_UNITARY2
+            as_complex[i, :m.size] = m.reshape(-1)
         else:
-            k = _KIND[kind]
-            p = np.ascontiguousarray(np.asarray(params, dtype=np.float64)) if params else None
-        pp = p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p is not None and p.size else None
-        check(L.sv_gate_make(k, q, pp, out[i:i + 1].ctypes.data))
+            kinds[i] = _KIND[kind]
+            if ps:
+                params[i, :len(ps)] = ps
+    check(lib().sv_gates_make(G, kinds.ctypes.data, qubits.ctypes.data, params.ctypes.data, 32, out.ctypes.data))
     return out
 
 

@@ -64,6 +64,7 @@ SV_COSTMODEL_PARAMS = 5313
 _VP = ctypes.c_void_p
 _SIGS = {
     "sv_gate_make": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _VP]),
+    "sv_gates_make": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int32, _VP]),
     "sv_options_default": (None, [ctypes.POINTER(sv_options)]),
     "sv_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
     "sv_destroy": (ctypes.c_int, [_VP]),

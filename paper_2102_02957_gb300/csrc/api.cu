@@ -1,7 +1,9 @@
 // C ABI entry points (include/sv.h): state handles, planning, execution and readouts.
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 
 #include "sv_internal.h"
 
@@ -90,6 +92,38 @@ struct BlockProg {
 // A section's width is its own where the plan chose one (steered plans), else the plan's.
 // Appended after the section programs: the composer's work lists, one per width (3, 4, 5 bits),
 // and the FP64 gate records they read.
+// Runs fn(0..count-1) on up to 8 host threads (on the calling thread alone for small counts).
+// fn must not throw except std::bad_alloc, which is passed on to the caller.
+template <typename F>
+static void parallel_for(int count, F fn) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = (int)std::max(1u, std::min(8u, std::min(hw ? hw : 1u, (unsigned)(count / 4))));
+    if (nth <= 1) {
+        for (int i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    std::atomic<bool> oom{false};
+    auto work = [&](int t) {
+        try {
+            for (int i = t; i < count; i += nth) fn(i);
+        } catch (const std::bad_alloc &) {
+            oom = true;
+        }
+    };
+    std::vector<std::thread> pool;
+    int started = 1;
+    try {
+        pool.reserve((size_t)nth);
+        for (; started < nth; ++started) pool.emplace_back(work, started);
+    } catch (...) {
+        // threads that could not start: their shares run on this thread
+    }
+    for (int t = started; t < nth; ++t) work(t);
+    work(0);
+    for (std::thread &th : pool) th.join();
+    if (oom) throw std::bad_alloc();
+}
+
 static int max_tc_segs(int r) { return r == 3 ? 24 : r == 4 ? 11 : 3; }
 
 static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r_plan, std::vector<unsigned char> &host,
@@ -102,27 +136,49 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r_p
     };
     std::vector<ComposeSeg> cs[3];  // per width 3, 4, 5
     std::vector<DevGate<double>> dg;
+    // each section's chunk layout, local gates and checks, in section order
+    struct Section {
+        size_t oi;
+        int r, width;
+        GatherLayout lay;
+        std::vector<BlockGate> gates;
+        std::vector<HostSeg> segs;
+    };
+    std::vector<Section> secs;
     for (size_t oi = 0; oi < plan->ops.size(); ++oi) {
         const PlanOp &op0 = plan->ops[oi];
         if (op0.kind != 2 && op0.kind != 4) continue;
-        const int r = op0.seg_bits ? op0.seg_bits : r_plan;
-        if (r < 3 || r > 5) fail(SV_ERR_PLAN, "tensor-core register groups have 3, 4 or 5 bits");
+        Section sc{};
+        sc.oi = oi;
+        sc.r = op0.seg_bits ? op0.seg_bits : r_plan;
+        if (sc.r < 3 || sc.r > 5) fail(SV_ERR_PLAN, "tensor-core register groups have 3, 4 or 5 bits");
+        sc.width = std::min(plan->c, plan->n);
+        if (op0.kind == 4) {
+            sc.lay = gather_layout(op0.mask, plan->n, 8);
+            sc.gates = localize_gates(op0, plan->n, plan->c, &sc.lay);
+            sc.width = sc.lay.ce;
+        } else {
+            sc.gates = localize_gates(op0, plan->n, plan->c, nullptr);
+        }
+        for (const BlockGate &g : sc.gates)
+            if (g.ext[0] >= 0 || g.ext[1] >= 0) fail(SV_ERR_PLAN, "tensor-core sections take no gates outside the chunk");
+        if (sc.width - plan->reserve < sc.r + 7) fail(SV_ERR_PLAN, "a section's chunk is too small for its register-group width");
+        secs.push_back(std::move(sc));
+    }
+    // register groups of every section (independent searches, spread over host threads; each
+    // section's result is its own, so the program does not depend on the threading)
+    parallel_for((int)secs.size(), [&](int i) {
+        Section &sc = secs[(size_t)i];
+        sc.segs = segment_block(sc.gates, sc.width, sc.r, 8);
+    });
+    for (const Section &sc : secs) {
+        const size_t oi = sc.oi;
+        const PlanOp &op0 = plan->ops[oi];
+        const int r = sc.r;
         const int kMaxTcSegs = max_tc_segs(r);
         const int b_bytes = tc_b_bytes(r);
-        int width = std::min(plan->c, plan->n);
-        GatherLayout lay{};
-        PlanOp local = op0;
-        if (op0.kind == 4) {
-            lay = gather_layout(op0.mask, plan->n, 8);
-            local.gates = localize_gates(op0, plan->n, plan->c, &lay);
-            width = lay.ce;
-        } else {
-            local.gates = localize_gates(op0, plan->n, plan->c, nullptr);
-        }
-        for (const BlockGate &g : local.gates)
-            if (g.ext[0] >= 0 || g.ext[1] >= 0) fail(SV_ERR_PLAN, "tensor-core sections take no gates outside the chunk");
-        if (width - plan->reserve < r + 7) fail(SV_ERR_PLAN, "a section's chunk is too small for its register-group width");
-        const std::vector<HostSeg> segs = segment_block(local.gates, width, r, 8);
+        const GatherLayout &lay = sc.lay;
+        const std::vector<HostSeg> &segs = sc.segs;
         for (size_t p0 = 0; p0 < segs.size(); p0 += kMaxTcSegs) {
             const size_t p1 = std::min(segs.size(), p0 + (size_t)kMaxTcSegs);
             BlockProg bp{};
@@ -156,7 +212,7 @@ static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r_p
                 c.g0 = (int32_t)dg.size();
                 for (int32_t gi : segs[k].gates) {
                     DevGate<double> g;
-                    const BlockGate &bg = local.gates[gi];
+                    const BlockGate &bg = sc.gates[gi];
                     encode_gate<double>(gates[bg.gi], bg, segs[k], g);
                     dg.push_back(g);
                 }
@@ -564,30 +620,31 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *gates, int64_t n_gates, s
         const bool tc = plan->use_tc && h->dtype == SV_C64 && std::min(plan->c, plan->n) - plan->reserve >= tc_bits + 7;
         size_t cs_off[3] = {0, 0, 0}, g_off = 0, flag_off = 0;
         int ncs[3] = {0, 0, 0};
+        // Tensor-core sections accumulate in FP32 with truncation, which shrinks every group's
+        // result by a few units in the last place, the same way each time: a bias that compounds
+        // over the circuit (norm 0.99981 after 450 quantum-volume gates at n = 30).  A unitary
+        // circuit keeps the norm, so when every fused group is unitary the state is rescaled to its
+        // input norm at the end: the radial error is removed, the unbiased rest stays.  The input
+        // norm is taken first, so that it runs while the host builds the programs.
+        const int nb_norm = reduce_blocks(h->n);
+        const bool renorm = tc && !plan->tc_no_renorm;
+        if (tc) ensure_scratch(h, (size_t)(2 * nb_norm + 2) * sizeof(double));
+        if (renorm) {
+            launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb_norm, h->stream);
+            ++st.kernel_launches;
+        }
         if (tc) build_programs_tc(plan, gates, tc_bits, host, progs, cs_off, ncs, g_off, flag_off);
         else if (h->dtype == SV_C64) build_programs<float>(plan, gates, seg_bits, host, progs);
         else build_programs<double>(plan, gates, seg_bits, host, progs);
         upload_program(h, host);
         const unsigned char *base = static_cast<const unsigned char *>(h->prog);
-        // Tensor-core sections accumulate in FP32 with truncation, which shrinks every group's
-        // result by a few units in the last place, the same way each time: a bias that compounds
-        // over the circuit (norm 0.99981 after 450 quantum-volume gates at n = 30).  A unitary
-        // circuit keeps the norm, so when every fused group is unitary the state is rescaled to its
-        // input norm at the end: the radial error is removed, the unbiased rest stays.
-        const int nb_norm = reduce_blocks(h->n);
         int *unitary_flag = tc ? reinterpret_cast<int *>(static_cast<unsigned char *>(h->prog) + flag_off) : nullptr;
-        const bool renorm = tc && !plan->tc_no_renorm;
         if (tc) {  // fuse every register group into its B operand, in FP64 on the GPU
-            ensure_scratch(h, (size_t)(2 * nb_norm + 2) * sizeof(double));
             for (int w = 0; w < 3; ++w)
                 if (ncs[w]) {
                     launch_compose(base + cs_off[w], ncs[w], base + g_off, h->prog, unitary_flag, w + 3, h->stream);
                     ++st.kernel_launches;
                 }
-        }
-        if (renorm) {
-            launch_partial_norm(h->dtype, h->amp, h->n, h->scratch, nb_norm, h->stream);
-            ++st.kernel_launches;
         }
         const uint64_t wait_ns = plan->wait_limit_ms > 0 ? (uint64_t)plan->wait_limit_ms * 1000000ull : kDefaultWaitNs;
         size_t bi = 0;

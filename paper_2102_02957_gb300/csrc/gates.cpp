@@ -124,3 +124,32 @@ extern "C" sv_status sv_gate_make(int32_t kind, const int32_t *qubits, const dou
         return e.code;
     }
 }
+
+// Many gate records in one call: entry i is sv_gate_make(kinds[i], qubits + 2 i,
+// params + i * param_stride, out + i), with NULL params for kinds that take none.
+extern "C" sv_status sv_gates_make(int64_t count, const int32_t *kinds, const int32_t *qubits, const double *params,
+                                   int32_t param_stride, sv_gate *out) {
+    if (count < 0 || param_stride < 0 || (count > 0 && (!kinds || !qubits || !out))) {
+        sv::set_error("sv_gates_make: negative count or stride, or null pointer");
+        return SV_ERR_ARG;
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        const int32_t k = kinds[i];
+        const int need = k == SV_K_UNITARY1 ? 8
+                         : k == SV_K_UNITARY2 ? 32
+                         : k == SV_K_U3       ? 3
+                         : (k == SV_K_RY || k == SV_K_RZ || k == SV_K_CP) ? 1
+                                                                          : 0;
+        if (need > param_stride || (need && !params)) {
+            sv::set_error("sv_gates_make: gate " + std::to_string(i) + ": its kind needs " + std::to_string(need) +
+                          " parameters per gate");
+            return SV_ERR_ARG;
+        }
+        const sv_status s = sv_gate_make(k, qubits + 2 * i, need ? params + i * (int64_t)param_stride : nullptr, out + i);
+        if (s != SV_OK) {
+            sv::set_error("sv_gates_make: gate " + std::to_string(i) + ": " + sv_last_error());
+            return s;
+        }
+    }
+    return SV_OK;
+}

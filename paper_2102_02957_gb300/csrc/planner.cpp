@@ -141,7 +141,27 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     // stops there with the same count.
     bool any_diag = false;
     for (const PG &g : remaining) any_diag = any_diag || g.diag;
+    // The first pending gates' qubit masks, packed for the look-ahead scans (refreshed per section).
+    std::vector<uint64_t> window;
     auto absorbed = [&](uint64_t chosen, size_t limit) {
+        if (!any_diag) {
+            // Without outside-chunk diagonals a gate is taken exactly when its qubits lie in the
+            // chunk qubits not yet blocked (`open`), and a gate left behind blocks the chunk
+            // qubits it touches.
+            uint64_t open = chosen;
+            int k = 0;
+            const size_t end = std::min(window.size(), limit);
+            for (size_t i = 0; i < end; ++i) {
+                const uint64_t v = window[i];
+                if ((v & ~open) == 0) {
+                    ++k;
+                } else if (v & chosen) {
+                    open &= ~v;
+                    if (!open) break;
+                }
+            }
+            return k;
+        }
         uint64_t blocked = 0, out_blocked = 0;
         int k = 0;
         for (size_t i = 0; i < remaining.size() && i < limit; ++i) {
@@ -160,6 +180,8 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     // and the first gate by the pending gate whose qubits add the most absorbable gates.
     auto greedy_select = [&](int tgt) {
         constexpr size_t kWindow = 512, kChoices = 64;
+        window.clear();
+        for (size_t i = 0; i < remaining.size() && i < kWindow; ++i) window.push_back(remaining[i].vmask);
         uint64_t chosen = remaining.front().vmask;
         for (int p = 0; p < pinned; ++p) chosen |= 1ull << pinv[p];
         while (popc(chosen) < tgt) {
@@ -167,8 +189,8 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             int best_score = -1;
             size_t tried = 0;
             std::vector<uint64_t> seen;
-            for (size_t i = 0; i < remaining.size() && i < kWindow && tried < kChoices; ++i) {
-                const uint64_t fresh = remaining[i].vmask & ~chosen;
+            for (size_t i = 0; i < window.size() && tried < kChoices; ++i) {
+                const uint64_t fresh = window[i] & ~chosen;
                 if (!fresh || popc(chosen | fresh) > tgt) continue;
                 if (std::find(seen.begin(), seen.end(), fresh) != seen.end()) continue;
                 seen.push_back(fresh);
@@ -399,7 +421,117 @@ constexpr int kGroupBeam = 8;
 constexpr int kGroupBeamMaxGates = 32;  // sections with more gates search with a beam of one
 constexpr int64_t kGroupSearchBudget = 4000000;  // pending-gate visits per section
 
+// The same search for sections of at most 64 gates, with each pending list held as the bit set of
+// its gate indices (a pending list keeps section order, so its set determines it): the split, the
+// duplicate check and the ranking then work on 64-bit words instead of index lists.
+bool beam_groups_small(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
+    const int G = (int)mask.size();
+    if (G == 0) return true;
+    bool any_zero = false;  // a gate with no chunk bit fits every group, so no scan may stop early
+    for (uint64_t mk : mask) any_zero = any_zero || mk == 0;
+    auto used_of = [&](uint64_t pend) {
+        uint64_t u = 0;
+        for (uint64_t p = pend; p; p &= p - 1) u |= mask[__builtin_ctzll(p)];
+        return u;
+    };
+    // the groups chosen so far, as a tree: each kept list points at its parent's entry
+    struct Chosen {
+        uint64_t set;
+        int parent;
+    };
+    std::vector<Chosen> tree;
+    auto finish = [&](int at, uint64_t last) {
+        out.clear();
+        for (int i = at; i >= 0; i = tree[(size_t)i].parent) out.push_back(tree[(size_t)i].set);
+        std::reverse(out.begin(), out.end());
+        out.push_back(last);
+        return true;
+    };
+    struct Node {
+        uint64_t pend;
+        int at;  // last chosen group in `tree`, -1 for none
+    };
+    // A level's children ranked as the search ranks them, found-first on ties.  Only the best
+    // `width` distinct lists survive a level, so they are kept as a sorted list of at most `width`
+    // while the level runs: a later duplicate of a list ties with it and comes after it, so it can
+    // neither displace it nor enter once the list has been pushed out.
+    struct Child {
+        uint64_t pend, set;
+        int parent, lb, npend, nbits;
+        int64_t order;
+    };
+    auto better = [](const Child &a, const Child &b) {
+        if (a.lb != b.lb) return a.lb < b.lb;
+        if (a.npend != b.npend) return a.npend < b.npend;
+        if (a.nbits != b.nbits) return a.nbits < b.nbits;
+        return a.order < b.order;
+    };
+    std::vector<Node> beam{Node{G == 64 ? ~0ull : (1ull << G) - 1, -1}};
+    std::vector<Child> top;
+    int64_t budget = kGroupSearchBudget;
+    while (true) {
+        top.clear();
+        int64_t found = 0;
+        for (const Node &nd : beam) {
+            const uint64_t used = used_of(nd.pend);
+            if (popc(used) <= r) return finish(nd.at, used);  // one more group takes every pending gate
+            const int npend = popc(nd.pend);
+            int bits[64], nb = 0;
+            for (int b = 0; b < 64; ++b)
+                if ((used >> b) & 1) bits[nb++] = b;
+            int sel[8];
+            for (int k = 0; k < r; ++k) sel[k] = k;
+            while (true) {
+                budget -= npend;
+                if (budget < 0) return false;
+                uint64_t set = 0;
+                for (int k = 0; k < r; ++k) set |= 1ull << bits[sel[k]];
+                uint64_t blocked = 0, rest = 0;
+                for (uint64_t p = nd.pend; p; p &= p - 1) {
+                    const int idx = __builtin_ctzll(p);
+                    const uint64_t mk = mask[idx];
+                    if ((mk & ~set) != 0 || (mk & blocked) != 0) {
+                        blocked |= mk;
+                        rest |= 1ull << idx;
+                        if (!any_zero && (blocked & set) == set) {  // nothing later fits
+                            rest |= p;
+                            break;
+                        }
+                    }
+                }
+                if (!rest) return finish(nd.at, set);
+                if (rest != nd.pend) {
+                    const int nbits = popc(used_of(rest));
+                    const Child ch{rest, set, nd.at, (nbits + r - 1) / r, popc(rest), nbits, found++};
+                    if ((int)top.size() < width || better(ch, top.back())) {
+                        bool dup = false;
+                        for (const Child &t : top) dup = dup || t.pend == rest;
+                        if (!dup) {
+                            size_t at = top.size();
+                            while (at > 0 && better(ch, top[at - 1])) --at;
+                            top.insert(top.begin() + (std::ptrdiff_t)at, ch);
+                            if ((int)top.size() > width) top.pop_back();
+                        }
+                    }
+                }
+                // next r-subset of [0, nb) in lexicographic order
+                int k = r - 1;
+                while (k >= 0 && sel[k] == nb - r + k) --k;
+                if (k < 0) break;
+                ++sel[k];
+                for (int q = k + 1; q < r; ++q) sel[q] = sel[q - 1] + 1;
+            }
+        }
+        beam.clear();
+        for (const Child &c : top) {
+            tree.push_back(Chosen{c.set, c.parent});
+            beam.push_back(Node{c.pend, (int)tree.size() - 1});
+        }
+    }
+}
+
 bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
+    if (mask.size() <= 64) return beam_groups_small(mask, r, out, width);
     struct Node {
         std::vector<int32_t> pend;
         std::vector<uint64_t> sets;

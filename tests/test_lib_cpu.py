@@ -71,6 +71,63 @@ def test_unitary_gate_roundtrip(sv):
     assert np.array_equal(rec["m"].view(np.complex128).reshape(4, 4), u)
 
 
+def _gate_one(sv, kind, qubits, params):
+    """One record through sv_gate_make (the single-gate entry point)."""
+    import ctypes
+    rec = np.zeros(1, dtype=sv.GATE_DTYPE)
+    q = (ctypes.c_int32 * 2)(*(list(qubits) + [0, 0])[:2])
+    if kind == "unitary":
+        m = np.ascontiguousarray(params[0], dtype=np.complex128)
+        k = sv._lib.SV_K_UNITARY1 if m.shape == (2, 2) else sv._lib.SV_K_UNITARY2
+        p = np.ascontiguousarray(m.reshape(-1).view(np.float64))
+    else:
+        k = sv._KIND[kind]
+        p = np.asarray(params, dtype=np.float64) if params else None
+    pp = p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p is not None else None
+    sv.check(sv.lib().sv_gate_make(k, q, pp, rec.ctypes.data))
+    return rec[0]
+
+
+def test_gates_make_batch_matches_single_calls(sv):
+    """sv_gates_make over a mixed list (every kind, 1- and 2-qubit unitaries) gives the records
+    sv_gate_make gives one at a time, and the oracle's matrices."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    descs = list(KINDS) + [("unitary", (4, 2), (cg.haar_unitary(rng),)),
+                           ("unitary", (5,), (np.array([[0, 1j], [1j, 0]]),))] + list(reversed(KINDS))
+    recs = sv.make_gates(descs)
+    assert len(recs) == len(descs)
+    for rec, (kind, qubits, params) in zip(recs, descs):
+        one = _gate_one(sv, kind, qubits, params)
+        assert rec.tobytes() == one.tobytes(), kind
+        if kind != "unitary":
+            order, m = og.matrix_of(kind, qubits, params)
+            nq = len(order)
+            got = rec["m"][: 2 * (1 << nq) ** 2].view(np.complex128).reshape(1 << nq, 1 << nq)
+            assert np.abs(got - m).max() < 1e-15
+    assert len(sv.make_gates([])) == 0
+
+
+def test_gates_make_batch_errors(sv):
+    L = sv.lib()
+    out = np.zeros(3, dtype=sv.GATE_DTYPE)
+    kinds = np.array([sv._KIND["h"], sv._KIND["cx"], sv._KIND["u3"]], dtype=np.int32)
+    qubits = np.array([[0, 0], [1, 1], [2, 0]], dtype=np.int32)  # gate 1 repeats a qubit
+    params = np.zeros((3, 32))
+    st = L.sv_gates_make(3, kinds.ctypes.data, qubits.ctypes.data, params.ctypes.data, 32, out.ctypes.data)
+    assert st == sv._lib.SV_ERR_ARG and "gate 1" in L.sv_last_error().decode()
+    assert out[0]["nq"] == 1 and out[2]["nq"] == 0  # entries before the failing one are written, later ones not
+    qubits[1] = (1, 2)
+    # a stride too short for U3's three angles, and parameters missing altogether
+    assert L.sv_gates_make(3, kinds.ctypes.data, qubits.ctypes.data, params.ctypes.data, 2, out.ctypes.data) \
+        == sv._lib.SV_ERR_ARG and "gate 2" in L.sv_last_error().decode()
+    assert L.sv_gates_make(3, kinds.ctypes.data, qubits.ctypes.data, None, 32, out.ctypes.data) == sv._lib.SV_ERR_ARG
+    assert L.sv_gates_make(2, kinds.ctypes.data, qubits.ctypes.data, None, 0, out.ctypes.data) == sv._lib.SV_OK
+    assert L.sv_gates_make(-1, kinds.ctypes.data, qubits.ctypes.data, None, 0, out.ctypes.data) == sv._lib.SV_ERR_ARG
+    assert L.sv_gates_make(1, None, qubits.ctypes.data, None, 0, out.ctypes.data) == sv._lib.SV_ERR_ARG
+    bad = np.array([99], dtype=np.int32)
+    assert L.sv_gates_make(1, bad.ctypes.data, qubits.ctypes.data, None, 0, out.ctypes.data) == sv._lib.SV_ERR_ARG
+
+
 def _circuits(n, seed):
     return [cg.random_layers(n, 4, seed), cg.quantum_volume(n, 4, seed), cg.qft(n), cg.hea(n, 2, seed, 1),
             cg.noisy_trajectory(n, 3, 0.3, seed, 2), cg.mirror(cg.quantum_volume(n, 2, seed + 1))]
