@@ -18,7 +18,6 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
-#include <unordered_map>
 
 #include "sv_internal.h"
 
@@ -403,37 +402,21 @@ void split_pending(const std::vector<uint64_t> &mask, const std::vector<int32_t>
     }
 }
 
-struct VecHash {
-    size_t operator()(const std::vector<int32_t> &v) const {
-        uint64_t h = 1469598103934665603ull;
-        for (int32_t x : v) h = (h ^ (uint64_t)(uint32_t)x) * 1099511628211ull;
-        return (size_t)h;
-    }
-};
-
 // Groups by beam search: level by level, every r-subset of the bits the pending gates use is
 // tried on each of the `width` pending lists kept (subsets in lexicographic order of their bit
 // positions); the children are ranked by the lower bound ceil(|bits used| / r) on the groups they
 // still need, then by pending gates, then by bits used (stable: ties keep the order they were
-// found in), and the first list to empty ends the search.  Returns false once the budget of
-// pending-gate visits is spent.
+// found in), and the first list to empty ends the search.  Returns false once the budget is spent
+// (each subset tried counts the length of the pending list it is tried on).
 constexpr int kGroupBeam = 8;
 constexpr int kGroupBeamMaxGates = 32;  // sections with more gates search with a beam of one
 constexpr int64_t kGroupSearchBudget = 4000000;  // pending-gate visits per section
 
-// The same search for sections of at most 64 gates, with each pending list held as the bit set of
-// its gate indices (a pending list keeps section order, so its set determines it): the split, the
-// duplicate check and the ranking then work on 64-bit words instead of index lists.
-bool beam_groups_small(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
+bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
     const int G = (int)mask.size();
     if (G == 0) return true;
     bool any_zero = false;  // a gate with no chunk bit fits every group, so no scan may stop early
     for (uint64_t mk : mask) any_zero = any_zero || mk == 0;
-    auto used_of = [&](uint64_t pend) {
-        uint64_t u = 0;
-        for (uint64_t p = pend; p; p &= p - 1) u |= mask[__builtin_ctzll(p)];
-        return u;
-    };
     // the groups chosen so far, as a tree: each kept list points at its parent's entry
     struct Chosen {
         uint64_t set;
@@ -448,15 +431,17 @@ bool beam_groups_small(const std::vector<uint64_t> &mask, int r, std::vector<uin
         return true;
     };
     struct Node {
-        uint64_t pend;
-        int at;  // last chosen group in `tree`, -1 for none
+        std::vector<int32_t> pend;
+        int at;  // its last group in `tree`, -1 for none
     };
-    // A level's children ranked as the search ranks them, found-first on ties.  Only the best
-    // `width` distinct lists survive a level, so they are kept as a sorted list of at most `width`
-    // while the level runs: a later duplicate of a list ties with it and comes after it, so it can
-    // neither displace it nor enter once the list has been pushed out.
+    // A level's children in rank order (lower bound, pending gates, bits used, then the order they
+    // were found in).  Only the best `width` distinct lists survive a level, so at most `width` are
+    // kept while the level runs: a later duplicate of a list ties with it and comes after it, so it
+    // can neither displace it nor enter once it has been pushed out.  A child's pending list is
+    // written out only when it enters.
     struct Child {
-        uint64_t pend, set;
+        std::vector<int32_t> pend;
+        uint64_t set;
         int parent, lb, npend, nbits;
         int64_t order;
     };
@@ -466,50 +451,76 @@ bool beam_groups_small(const std::vector<uint64_t> &mask, int r, std::vector<uin
         if (a.nbits != b.nbits) return a.nbits < b.nbits;
         return a.order < b.order;
     };
-    std::vector<Node> beam{Node{G == 64 ? ~0ull : (1ull << G) - 1, -1}};
+    std::vector<Node> beam(1);
+    beam[0].pend.resize((size_t)G);
+    std::iota(beam[0].pend.begin(), beam[0].pend.end(), 0);
+    beam[0].at = -1;
     std::vector<Child> top;
+    std::vector<uint64_t> suffix;  // suffix[j]: the bits of pend[j..]
     int64_t budget = kGroupSearchBudget;
     while (true) {
         top.clear();
         int64_t found = 0;
         for (const Node &nd : beam) {
-            const uint64_t used = used_of(nd.pend);
+            const std::vector<int32_t> &pend = nd.pend;
+            const int P = (int)pend.size();
+            suffix.assign((size_t)P + 1, 0);
+            for (int j = P - 1; j >= 0; --j) suffix[(size_t)j] = suffix[(size_t)j + 1] | mask[(size_t)pend[(size_t)j]];
+            const uint64_t used = suffix[0];
             if (popc(used) <= r) return finish(nd.at, used);  // one more group takes every pending gate
-            const int npend = popc(nd.pend);
             int bits[64], nb = 0;
             for (int b = 0; b < 64; ++b)
                 if ((used >> b) & 1) bits[nb++] = b;
             int sel[8];
             for (int k = 0; k < r; ++k) sel[k] = k;
             while (true) {
-                budget -= npend;
+                budget -= P;
                 if (budget < 0) return false;
                 uint64_t set = 0;
                 for (int k = 0; k < r; ++k) set |= 1ull << bits[sel[k]];
-                uint64_t blocked = 0, rest = 0;
-                for (uint64_t p = nd.pend; p; p &= p - 1) {
-                    const int idx = __builtin_ctzll(p);
-                    const uint64_t mk = mask[idx];
-                    if ((mk & ~set) != 0 || (mk & blocked) != 0) {
+                // the gates the group takes, and the bits of those it leaves (once every bit of the
+                // group is blocked nothing later fits, and the rest of the list is left as it is)
+                uint64_t blocked = 0, left = 0;
+                int taken = 0, stop = P;
+                for (int j = 0; j < P; ++j) {
+                    const uint64_t mk = mask[(size_t)pend[(size_t)j]];
+                    if ((mk & ~set) == 0 && (mk & blocked) == 0) {
+                        ++taken;
+                    } else {
                         blocked |= mk;
-                        rest |= 1ull << idx;
-                        if (!any_zero && (blocked & set) == set) {  // nothing later fits
-                            rest |= p;
+                        left |= mk;
+                        if (!any_zero && (blocked & set) == set) {
+                            stop = j + 1;
                             break;
                         }
                     }
                 }
-                if (!rest) return finish(nd.at, set);
-                if (rest != nd.pend) {
-                    const int nbits = popc(used_of(rest));
-                    const Child ch{rest, set, nd.at, (nbits + r - 1) / r, popc(rest), nbits, found++};
+                if (taken == P) return finish(nd.at, set);
+                if (taken > 0) {
+                    Child ch;
+                    ch.set = set;
+                    ch.parent = nd.at;
+                    ch.nbits = popc(left | suffix[(size_t)stop]);
+                    ch.lb = (ch.nbits + r - 1) / r;
+                    ch.npend = P - taken;
+                    ch.order = found++;
                     if ((int)top.size() < width || better(ch, top.back())) {
+                        ch.pend.reserve((size_t)ch.npend);
+                        blocked = 0;
+                        for (int j = 0; j < stop; ++j) {
+                            const uint64_t mk = mask[(size_t)pend[(size_t)j]];
+                            if ((mk & ~set) != 0 || (mk & blocked) != 0) {
+                                blocked |= mk;
+                                ch.pend.push_back(pend[(size_t)j]);
+                            }
+                        }
+                        ch.pend.insert(ch.pend.end(), pend.begin() + stop, pend.end());
                         bool dup = false;
-                        for (const Child &t : top) dup = dup || t.pend == rest;
+                        for (const Child &t : top) dup = dup || t.pend == ch.pend;
                         if (!dup) {
                             size_t at = top.size();
                             while (at > 0 && better(ch, top[at - 1])) --at;
-                            top.insert(top.begin() + (std::ptrdiff_t)at, ch);
+                            top.insert(top.begin() + (std::ptrdiff_t)at, std::move(ch));
                             if ((int)top.size() > width) top.pop_back();
                         }
                     }
@@ -523,86 +534,10 @@ bool beam_groups_small(const std::vector<uint64_t> &mask, int r, std::vector<uin
             }
         }
         beam.clear();
-        for (const Child &c : top) {
+        for (Child &c : top) {
             tree.push_back(Chosen{c.set, c.parent});
-            beam.push_back(Node{c.pend, (int)tree.size() - 1});
+            beam.push_back(Node{std::move(c.pend), (int)tree.size() - 1});
         }
-    }
-}
-
-bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
-    if (mask.size() <= 64) return beam_groups_small(mask, r, out, width);
-    struct Node {
-        std::vector<int32_t> pend;
-        std::vector<uint64_t> sets;
-    };
-    auto used_of = [&](const std::vector<int32_t> &pend) {
-        uint64_t u = 0;
-        for (int32_t idx : pend) u |= mask[idx];
-        return u;
-    };
-    std::vector<Node> beam(1);
-    beam[0].pend.resize(mask.size());
-    std::iota(beam[0].pend.begin(), beam[0].pend.end(), 0);
-    if (beam[0].pend.empty()) return true;
-    int64_t budget = kGroupSearchBudget;
-    std::vector<int32_t> rest;
-    while (true) {
-        struct Child {
-            Node node;
-            int lb, npend, nbits;
-        };
-        std::vector<Child> children;
-        std::unordered_map<std::vector<int32_t>, int, VecHash> seen;
-        for (const Node &nd : beam) {
-            const uint64_t used = used_of(nd.pend);
-            if (popc(used) <= r) {  // one more group takes every pending gate
-                out = nd.sets;
-                out.push_back(used);
-                return true;
-            }
-            int bits[64], nb = 0;
-            for (int b = 0; b < 64; ++b)
-                if ((used >> b) & 1) bits[nb++] = b;
-            int sel[8];
-            for (int k = 0; k < r; ++k) sel[k] = k;
-            while (true) {
-                budget -= (int64_t)nd.pend.size();
-                if (budget < 0) return false;
-                uint64_t set = 0;
-                for (int k = 0; k < r; ++k) set |= 1ull << bits[sel[k]];
-                split_pending(mask, nd.pend, set, nullptr, rest);
-                if (rest.empty()) {
-                    out = nd.sets;
-                    out.push_back(set);
-                    return true;
-                }
-                if (rest.size() < nd.pend.size() && seen.emplace(rest, 0).second) {
-                    Child ch;
-                    ch.node.pend = rest;
-                    ch.node.sets = nd.sets;
-                    ch.node.sets.push_back(set);
-                    ch.nbits = popc(used_of(rest));
-                    ch.lb = (ch.nbits + r - 1) / r;
-                    ch.npend = (int)rest.size();
-                    children.push_back(std::move(ch));
-                }
-                // next r-subset of [0, nb) in lexicographic order
-                int k = r - 1;
-                while (k >= 0 && sel[k] == nb - r + k) --k;
-                if (k < 0) break;
-                ++sel[k];
-                for (int q = k + 1; q < r; ++q) sel[q] = sel[q - 1] + 1;
-            }
-        }
-        std::stable_sort(children.begin(), children.end(), [](const Child &a, const Child &b) {
-            if (a.lb != b.lb) return a.lb < b.lb;
-            if (a.npend != b.npend) return a.npend < b.npend;
-            return a.nbits < b.nbits;
-        });
-        if (children.size() > (size_t)width) children.resize((size_t)width);
-        beam.clear();
-        for (Child &c : children) beam.push_back(std::move(c.node));
     }
 }
 
