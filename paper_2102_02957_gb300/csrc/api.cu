@@ -86,12 +86,6 @@ struct BlockProg {
     bool gathered = false;
 };
 
-// Tensor-core programs: every register group (r bits) of a section becomes one fused unitary.  A
-// section whose B operands (tc_b_bytes(r) per group: 2, 8 or 32 KiB) would not fit next to the
-// chunk ring in shared memory is split into consecutive sweeps of at most max_tc_segs(r) groups.
-// A section's width is its own where the plan chose one (steered plans), else the plan's.
-// Appended after the section programs: the composer's work lists, one per width (3, 4, 5 bits),
-// and the FP64 gate records they read.
 // Runs fn(0..count-1) on up to 8 host threads (on the calling thread alone for small counts).
 // fn must not throw except std::bad_alloc, which is passed on to the caller.
 template <typename F>
@@ -124,6 +118,12 @@ static void parallel_for(int count, F fn) {
     if (oom) throw std::bad_alloc();
 }
 
+// Tensor-core programs: every register group (r bits) of a section becomes one fused unitary.  A
+// section whose B operands (tc_b_bytes(r) per group: 2, 8 or 32 KiB) would not fit next to the
+// chunk ring in shared memory is split into consecutive sweeps of at most max_tc_segs(r) groups.
+// A section's width is its own where the plan chose one (steered plans), else the plan's.
+// Appended after the section programs: the composer's work lists, one per width (3, 4, 5 bits),
+// and the FP64 gate records they read.
 static int max_tc_segs(int r) { return r == 3 ? 24 : r == 4 ? 11 : 3; }
 
 static void build_programs_tc(const sv_plan *plan, const sv_gate *gates, int r_plan, std::vector<unsigned char> &host,
