@@ -128,39 +128,20 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         for (int p = 0; p < (pinned ? n : width) && cnt < tgt; ++p) try_add(1ull << pinv[p]);
         return chosen;
     };
-    // Gates of REMAINING (at most `limit` inspected) that a section on `chosen` would take.
     // Whether the QB_BLOCKED scan takes gate g into a section on `chosen` (see the scan below).
     auto takes = [&](const PG &g, uint64_t chosen, uint64_t blocked, uint64_t out_blocked) {
         const uint64_t outside = g.vmask & ~chosen;
         return outside == 0 ? (g.vmask & blocked) == 0
                             : g.diag && (g.vmask & chosen & blocked) == 0 && (outside & out_blocked) == 0;
     };
-    // Once every chunk qubit is blocked no later gate is taken (each touches a chunk qubit, unless
-    // it is a diagonal gate wholly outside the chunk, possible with diag_outside only), so the scan
-    // stops there with the same count.
+    // whether some gate may join a section with qubits outside the chunk (diag_outside)
     bool any_diag = false;
     for (const PG &g : remaining) any_diag = any_diag || g.diag;
     // The first pending gates' qubit masks, packed for the look-ahead scans (refreshed per section).
     std::vector<uint64_t> window;
+    // Gates of REMAINING (at most `limit` inspected) that a section on `chosen` would take: the
+    // scan in full, for plans with outside-chunk diagonals.
     auto absorbed = [&](uint64_t chosen, size_t limit) {
-        if (!any_diag) {
-            // Without outside-chunk diagonals a gate is taken exactly when its qubits lie in the
-            // chunk qubits not yet blocked (`open`), and a gate left behind blocks the chunk
-            // qubits it touches.
-            uint64_t open = chosen;
-            int k = 0;
-            const size_t end = std::min(window.size(), limit);
-            for (size_t i = 0; i < end; ++i) {
-                const uint64_t v = window[i];
-                if ((v & ~open) == 0) {
-                    ++k;
-                } else if (v & chosen) {
-                    open &= ~v;
-                    if (!open) break;
-                }
-            }
-            return k;
-        }
         uint64_t blocked = 0, out_blocked = 0;
         int k = 0;
         for (size_t i = 0; i < remaining.size() && i < limit; ++i) {
@@ -170,8 +151,58 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
             } else {
                 if (g.vmask & chosen) blocked |= g.vmask;
                 out_blocked |= g.vmask & ~chosen;
-                if (!any_diag && (blocked & chosen) == chosen) break;
             }
+        }
+        return k;
+    };
+    // Without outside-chunk diagonals a gate is taken exactly when its qubits lie in the chunk
+    // qubits not yet blocked (`open`), a gate left behind blocks the chunk qubits it touches, and
+    // once every chunk qubit is blocked no later gate is taken, so the scan stops there.  The scan
+    // for `chosen | fresh` runs exactly as the scan for `chosen` (with the qubits of `fresh` open
+    // besides) up to the first gate that touches `fresh`:
+    // gates before it neither use nor block those qubits.  So the scan of `chosen` is kept
+    // position by position (the count so far and the open qubits before each position, frozen
+    // once it stops) and a candidate's scan starts at the first use of its new qubits.
+    std::vector<int> base_k;
+    std::vector<uint64_t> base_open;
+    int first_use[64];
+    auto scan_base = [&](uint64_t chosen) {
+        const size_t W = window.size();
+        base_k.resize(W + 1);
+        base_open.resize(W + 1);
+        uint64_t open = chosen;
+        int k = 0;
+        size_t t = 0;
+        for (; t < W; ++t) {
+            base_k[t] = k;
+            base_open[t] = open;
+            const uint64_t v = window[t];
+            const bool take = (v & ~open) == 0;
+            k += take;
+            open &= ~(v & (0 - (uint64_t)(!take && (v & chosen) != 0)));
+            if (!open) {
+                ++t;
+                break;
+            }
+        }
+        for (; t <= W; ++t) {
+            base_k[t] = k;
+            base_open[t] = open;
+        }
+    };
+    auto absorbed_with = [&](uint64_t chosen, uint64_t fresh) {
+        const size_t W = window.size();
+        size_t t0 = W;
+        for (uint64_t f = fresh; f; f &= f - 1) t0 = std::min(t0, (size_t)first_use[__builtin_ctzll(f)]);
+        const uint64_t ch = chosen | fresh;
+        uint64_t open = base_open[t0] | fresh;
+        int k = base_k[t0];
+        for (size_t i = t0; i < W; ++i) {  // the scan above, without data-dependent branches
+            const uint64_t v = window[i];
+            const bool take = (v & ~open) == 0;
+            k += take;
+            open &= ~(v & (0 - (uint64_t)(!take && (v & ch) != 0)));
+            if (!open) break;
         }
         return k;
     };
@@ -181,20 +212,30 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
         constexpr size_t kWindow = 512, kChoices = 64;
         window.clear();
         for (size_t i = 0; i < remaining.size() && i < kWindow; ++i) window.push_back(remaining[i].vmask);
+        for (int b = 0; b < 64; ++b) first_use[b] = (int)window.size();
+        for (size_t i = window.size(); i-- > 0;)
+            for (uint64_t v = window[i]; v; v &= v - 1) first_use[__builtin_ctzll(v)] = (int)i;
         uint64_t chosen = remaining.front().vmask;
         for (int p = 0; p < pinned; ++p) chosen |= 1ull << pinv[p];
+        uint64_t seen[64];  // the new-qubit sets tried, one bit per pair (lower qubit, higher qubit)
         while (popc(chosen) < tgt) {
             uint64_t best = 0;
             int best_score = -1;
             size_t tried = 0;
-            std::vector<uint64_t> seen;
+            std::memset(seen, 0, sizeof(seen));
+            if (!any_diag) scan_base(chosen);
+            const int room = tgt - popc(chosen);
             for (size_t i = 0; i < window.size() && tried < kChoices; ++i) {
                 const uint64_t fresh = window[i] & ~chosen;
-                if (!fresh || popc(chosen | fresh) > tgt) continue;
-                if (std::find(seen.begin(), seen.end(), fresh) != seen.end()) continue;
-                seen.push_back(fresh);
+                if (!fresh) continue;
+                // a gate has at most two qubits
+                const uint64_t rest = fresh & (fresh - 1);
+                if ((rest ? 2 : 1) > room) continue;
+                const int lo = __builtin_ctzll(fresh), hi = rest ? __builtin_ctzll(rest) : lo;
+                if ((seen[lo] >> hi) & 1) continue;
+                seen[lo] |= 1ull << hi;
                 ++tried;
-                const int sc = absorbed(chosen | fresh, kWindow);
+                const int sc = any_diag ? absorbed(chosen | fresh, kWindow) : absorbed_with(chosen, fresh);
                 if (sc > best_score) {
                     best_score = sc;
                     best = fresh;
