@@ -379,6 +379,80 @@ def test_register_group_search_bounds(sv, name, c, pinned):
     assert bound <= got <= greedy
 
 
+def _beam_groups(masks, r, width, budget=4_000_000):
+    """Register groups by beam search, written out plainly: level by level every r-subset of the
+    bits the pending gates use (lexicographic in bit position) is tried on every kept pending
+    list; a child that takes at least one gate and whose pending list was not produced before on
+    this level is kept; children are ranked by ceil(bits used / r), then pending gates, then bits
+    used, ties in the order found; the best `width` survive; the first subset that empties a
+    list, or a list whose bits fit one group, ends the search.  None once the budget (the pending
+    list's length per subset tried) is spent."""
+    from itertools import combinations
+
+    def split(pend, bits):
+        blocked, rest = 0, []
+        for i in pend:
+            if (masks[i] & ~bits) == 0 and (masks[i] & blocked) == 0:
+                continue
+            blocked |= masks[i]
+            rest.append(i)
+        return rest
+
+    def used_of(pend):
+        u = 0
+        for i in pend:
+            u |= masks[i]
+        return u
+
+    if not masks:
+        return 0
+    beam = [(list(range(len(masks))), 0)]  # (pending list, groups so far)
+    while True:
+        children, seen = [], set()
+        for pend, ngroups in beam:
+            used = used_of(pend)
+            if bin(used).count("1") <= r:
+                return ngroups + 1
+            bits = [b for b in range(64) if (used >> b) & 1]
+            for sub in combinations(bits, r):
+                budget -= len(pend)
+                if budget < 0:
+                    return None
+                rest = split(pend, sum(1 << b for b in sub))
+                if not rest:
+                    return ngroups + 1
+                if len(rest) < len(pend) and tuple(rest) not in seen:
+                    seen.add(tuple(rest))
+                    nbits = bin(used_of(rest)).count("1")
+                    children.append(((-(-nbits // r), len(rest), nbits), rest, ngroups + 1))
+        children.sort(key=lambda ch: ch[0])  # stable: ties keep the order found
+        beam = [(rest, ng) for _key, rest, ng in children[:width]]
+
+
+@pytest.mark.parametrize("name,c", [("qv26", 12), ("rl16", 10), ("qft28", 12), ("rl28", 12), ("qv30", 12)])
+def test_register_group_search_matches_restatement(sv, name, c):
+    """The library's register-group count (paper layout: chunk bits 0..c-1, 4-bit groups) equals
+    the plain beam search above section by section, summed over the plan (beam of 8 for sections
+    of up to 32 gates, of 1 above; greedy growth where the search runs out of budget)."""
+    w = cg.WORKLOADS[name]
+    desc = cg.build(name)
+    n = w["n"]
+    lib_plan = sv.Plan(n, sv.make_gates(desc), chunk_bits=c)
+    oracle_plan = planner.plan_blocking(n, desc, c)
+    total = 0
+    for _bits, gl in oracle_plan.blocks():
+        masks = []
+        for _gi, phys in gl:
+            m = 0
+            for q in phys:
+                if 0 <= q < c:
+                    m |= 1 << q
+            masks.append(m)
+        got = _beam_groups(masks, min(4, c, n), 8 if len(masks) <= 32 else 1)
+        total += got if got is not None else _greedy_groups(masks, min(4, c, n))
+    assert lib_plan.info().n_segments == total
+
+
 def test_plan_widths_arguments(sv):
     """sv_plan_get_widths: null plan or count and a negative capacity are argument errors; a
     capacity smaller than the section count fills what fits and still reports the count."""
