@@ -451,7 +451,7 @@ void split_pending(const std::vector<uint64_t> &mask, const std::vector<int32_t>
 // (each subset tried counts the length of the pending list it is tried on).
 constexpr int kGroupBeam = 8;
 constexpr int kGroupBeamMaxGates = 32;  // sections with more gates search with a beam of one
-constexpr int64_t kGroupSearchBudget = 4000000;  // pending-gate visits per section
+constexpr int64_t kGroupSearchBudget = 4000000;  // per section: pending-list length summed over the subsets tried
 
 bool beam_groups(const std::vector<uint64_t> &mask, int r, std::vector<uint64_t> &out, int width) {
     const int G = (int)mask.size();
