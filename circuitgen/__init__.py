@@ -104,8 +104,9 @@ _PAULI_1Q = ("x", "y", "z")
 def noisy_trajectory(n: int, depth: int, p: float, seed: int, traj_id: int):
     """One depolarizing-noise trajectory of the random-layer circuit: after each gate, with
     probability p, a uniform non-identity Pauli on the gate's qubits (3 choices for a 1-qubit
-    gate, 15 for a 2-qubit gate), drawn from a generator seeded with seed XOR traj_id.  The
-    trajectory is a plain deterministic circuit that both sides replay."""
+    gate, 15 for a 2-qubit gate), drawn from a generator seeded with
+    seed XOR (traj_id * 0x9E3779B1 + 1).  The trajectory is a plain deterministic circuit that
+    both sides replay."""
     base = random_layers(n, depth, seed * 1000003 + n)
     rng = _rng(seed ^ (traj_id * 0x9E3779B1 + 1))
     gates = []
