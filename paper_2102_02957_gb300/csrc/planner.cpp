@@ -159,10 +159,10 @@ sv_plan *plan_blocking(int n, const sv_gate *gates, int64_t n_gates, const sv_op
     // qubits not yet blocked (`open`), a gate left behind blocks the chunk qubits it touches, and
     // once every chunk qubit is blocked no later gate is taken, so the scan stops there.  The scan
     // for `chosen | fresh` runs exactly as the scan for `chosen` (with the qubits of `fresh` open
-    // besides) up to the first gate that touches `fresh`:
-    // gates before it neither use nor block those qubits.  So the scan of `chosen` is kept
-    // position by position (the count so far and the open qubits before each position, frozen
-    // once it stops) and a candidate's scan starts at the first use of its new qubits.
+    // besides) up to the first gate that touches `fresh`, since the gates before it neither use
+    // nor block those qubits.  So the scan of `chosen` is kept position by position (the count so
+    // far and the open qubits before each position, frozen once it stops) and a candidate's scan
+    // starts at the first use of its new qubits.
     std::vector<int> base_k;
     std::vector<uint64_t> base_open;
     int first_use[64];
